@@ -1,0 +1,239 @@
+/*
+ * floquet_sv.h -- C ABI of the GB300 state-vector simulator for driven spin
+ * chains (arXiv 2111.08044, "Simulation of quantum many-body dynamics with
+ * Tensor Processing Units: Floquet prethermalization").
+ *
+ * The library evolves the full 2^L complex amplitude vector of an open chain
+ * of L spin-1/2 sites by repeated application of a Floquet unitary,
+ * |psi(nT)> = U_F^n |psi(0)> (Eq. 3), and measures the energy density
+ * <psi|H0|psi>/L once per period (Eq. 10 with H0 the time-averaged
+ * Hamiltonian of Eq. 7).
+ *
+ * Conventions shared by every call:
+ *   - Site i is bit i of the amplitude index (little-endian).  A two-site
+ *     operator on bond (i, i+1) is a row-major 4x4 matrix with local index
+ *     r = 2*b_i + b_{i+1} (site i is the high bit), as in the contraction
+ *     U_{b7 b8 alpha beta} of Eq. 2.
+ *   - |0> is spin up: Z|0> = +|0>.
+ *   - One period: K Trotter steps, each all gates on bonds of parity
+ *     `first_layer` then all gates on the other parity (the two-layer
+ *     brickwork of Eq. 4), every gate exp(-i tau h_b) (Eq. 5) with tau = T/K
+ *     and h_b = J Z_i Z_{i+1} + c_x(i) X_i + c_x(i+1) X_{i+1}
+ *                             + c_z(i) Z_i + c_z(i+1) Z_{i+1},
+ *     where each bond gives each of its sites h/2 of the on-site fields,
+ *     except that an open end site receives edge_field_weight * h from its
+ *     one bond; then the kick exp(-i theta sum_i X_i).
+ *   - H0 = sum_b h_b (Eq. 7).  Energies are of the unnormalised state; the
+ *     squared norm is reported beside them.
+ *   - Status: every call returns SV_OK (0) or a negative SV_E* code; no
+ *     exception or abort crosses this boundary.  sv_last_error() gives text.
+ *   - Memory: the state buffer belongs to the caller (device memory, e.g. a
+ *     torch tensor).  The library allocates only small device buffers
+ *     (gate tables, fused unitaries, reduction partials, the energy ring).
+ *   - Streams: every launch goes to the stream given at sv_create, in call
+ *     order.  Calls with host outputs synchronise that stream before
+ *     returning.
+ */
+#ifndef FLOQUET_SV_H
+#define FLOQUET_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SV_OK 0
+#define SV_EINVAL (-1)      /* bad argument (size, range, null pointer) */
+#define SV_ENOMEM (-2)      /* a library allocation failed */
+#define SV_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed */
+#define SV_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define SV_ESTATE (-5)      /* calls made in the wrong order */
+#define SV_EUNSUPPORTED (-6) /* valid request this build does not implement */
+
+/* state precision */
+#define SV_C64 0  /* complex64 amplitudes, FP32 arithmetic, FP64 reductions */
+#define SV_C128 1 /* complex128 amplitudes, FP64 arithmetic (check mode) */
+
+/* evolution form */
+#define SV_MODE_PLAIN 0 /* one kernel pass per two-qubit gate */
+#define SV_MODE_BLOCK 1 /* fused n-qubit blocks on the tensor cores */
+
+/* arithmetic of the block form */
+#define SV_SPLIT_TF32X3 0 /* hi/lo TF32 operands, 3 products, FP32 accumulate */
+#define SV_SPLIT_FP32 1   /* FP32 CUDA-core block apply (reference form) */
+
+typedef struct sv_ctx sv_ctx;
+
+/* Parameters of the driven chain and of the evolution form. */
+typedef struct sv_floquet_params {
+  double J;                 /* Z Z coupling */
+  double hx;                /* transverse field */
+  double hz;                /* longitudinal field */
+  double T;                 /* Floquet period */
+  double theta;             /* kick angle: kick = exp(-i theta sum X) */
+  double edge_field_weight; /* field share of an open end site (0.5: uniform) */
+  int32_t K;                /* Trotter steps per period, >= 1 */
+  int32_t first_layer;      /* 0: bonds (0,1),(2,3),.. first; 1: odd bonds first */
+  int32_t mode;             /* SV_MODE_PLAIN or SV_MODE_BLOCK */
+  int32_t block_n;          /* block width n for SV_MODE_BLOCK (2..7); 0 = default */
+  int32_t split;            /* SV_SPLIT_* (block mode) */
+  int32_t renorm_every;     /* rescale psi to unit norm every this many periods; 0 = never */
+  int64_t n_period_params;  /* > 0: theta_p / hx_p give one value per period */
+  const double *theta_p;    /* host, length n_period_params, or NULL */
+  const double *hx_p;       /* host, length n_period_params, or NULL */
+} sv_floquet_params;
+
+/* Library version (an integer that grows with the ABI). */
+int sv_version(void);
+
+/*
+ * Create a context on CUDA device `device` for amplitudes of the given
+ * precision (SV_C64 or SV_C128).  `cuda_stream` is a cudaStream_t (NULL:
+ * the legacy default stream).  *out receives the handle; free it with
+ * sv_destroy.  Errors: SV_EINVAL (bad precision / null out), SV_ECUDA (no
+ * such device), SV_ENOMEM.
+ */
+int sv_create(sv_ctx **out, int device, int precision, void *cuda_stream);
+
+/*
+ * Attach the caller's device buffer that holds the state: at least
+ * 8*2^L bytes (SV_C64) or 16*2^L bytes (SV_C128), 256-byte aligned,
+ * interleaved (re, im).  The caller keeps ownership and must keep it alive
+ * while the context uses it.  Errors: SV_EINVAL (null or misaligned).
+ */
+int sv_attach_state(sv_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/*
+ * Write the product state psi_x = prod_i s_i[b_i(x)] (a product initial
+ * state, cf. Eq. 9) into the attached buffer.  product_state: host array of
+ * 4*L doubles, per site (re a, im a, re b, im b) with a the |0> and b the
+ * |1> component; the library normalises each site.  Resets the period
+ * counter to 0.  L: 2..34 (SV_C64), 2..33 (SV_C128).  Errors: SV_EINVAL
+ * (L out of range, buffer too small, zero spinor), SV_ESTATE (no buffer).
+ */
+int sv_init(sv_ctx *ctx, int L, const double *product_state);
+
+/*
+ * Build the period: FP64 bond gates exp(-i tau h_b) (Eq. 5), kick folding
+ * into the last gate on each site, and, in block mode, the fusion of gates
+ * into n-qubit block unitaries (the >= 7-qubit operators of Sec. II, built
+ * here in FP64).  Uploads everything the evolution needs.  Requires
+ * sv_init.  Per-period parameters (n_period_params > 0) are supported in
+ * plain mode only.  Errors: SV_EINVAL, SV_ESTATE, SV_EUNSUPPORTED,
+ * SV_ENOMEM, SV_ECUDA.
+ */
+int sv_build_floquet(sv_ctx *ctx, const sv_floquet_params *p);
+
+/*
+ * Apply `periods` periods (Eq. 3).  After each period the energy density
+ * <psi|H0|psi>/L and <psi|psi> are recorded; energy_out / norm_out (host,
+ * length `periods`, either may be NULL) receive them.  With per-period
+ * parameters the period counter must stay below n_period_params.
+ * Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA.
+ */
+int sv_evolve(sv_ctx *ctx, int64_t periods, double *energy_out, double *norm_out);
+
+/*
+ * sv_evolve without the CUDA graph, for measurement: every kernel launch of
+ * a period is bracketed by CUDA events on the context's stream, and
+ * pass_ms[k] (host, length launches_per_period from sv_pass_info, nullable)
+ * accumulates the duration of launch k of the period over all periods, in
+ * milliseconds.  Results are identical to sv_evolve.  Errors as sv_evolve.
+ */
+int sv_evolve_profiled(sv_ctx *ctx, int64_t periods, double *energy_out,
+                       double *norm_out, double *pass_ms);
+
+/*
+ * Energy density <psi|H0|psi>/L (Eq. 10 / L) and <psi|psi> of the current
+ * state (host outputs; either may be NULL).  Errors: SV_ESTATE, SV_ECUDA.
+ */
+int sv_expect_energy(sv_ctx *ctx, double *energy_density, double *norm2);
+
+/* Scale psi to unit norm (FP64 norm); *norm2_before (nullable) gets the
+ * squared norm it had.  Errors: SV_ESTATE, SV_ECUDA. */
+int sv_renormalize(sv_ctx *ctx, double *norm2_before);
+
+/*
+ * Reverse-mode gradient of the final energy density f = <psi_P|H0|psi_P>/L
+ * with respect to the per-period kick angles theta_p and fields hx_p
+ * (p = 0..P-1, P = n_period_params, plain mode).  Starting from the current
+ * state it evolves P periods forward without storing states, seeds
+ * lambda = (H0/L) psi_P, and walks the gates backwards, un-applying each on
+ * psi and lambda while accumulating 2 Re <lambda| dG G^dagger |psi>.  On
+ * return the state buffer holds psi back at its starting point up to
+ * rounding.  grad_theta / grad_hx: host, length P (nullable).
+ * energy_density (nullable): f.  Needs 2x the state memory for lambda,
+ * allocated by the library.  Errors: SV_EINVAL, SV_ESTATE, SV_ENOMEM,
+ * SV_ECUDA, SV_EUNSUPPORTED.
+ */
+int sv_adjoint(sv_ctx *ctx, double *grad_theta, double *grad_hx,
+               double *energy_density);
+
+/* Copy the state to host memory (bytes >= state size).  Errors: SV_EINVAL,
+ * SV_ESTATE, SV_ECUDA. */
+int sv_get_state(sv_ctx *ctx, void *host_dst, size_t bytes);
+
+/* Copy a state from host memory into the attached buffer (for checkpoint
+ * resume); sets the period counter.  Errors as sv_get_state. */
+int sv_set_state(sv_ctx *ctx, const void *host_src, size_t bytes, int64_t period);
+
+/* Periods applied since sv_init / sv_set_state. */
+int64_t sv_period_counter(const sv_ctx *ctx);
+
+/*
+ * Kernel passes over the state per period and two-qubit gates per period
+ * of the built evolution (for throughput accounting).  Errors: SV_ESTATE.
+ */
+int sv_pass_info(const sv_ctx *ctx, int *passes_per_period, int *gates_per_period,
+                 int *launches_per_period);
+
+/* Bytes the last sv_build_floquet copied host -> device (gate tables, fused
+ * unitaries, tensor-core operands).  Errors: SV_ESTATE. */
+int sv_build_bytes(const sv_ctx *ctx, size_t *h2d_bytes);
+
+/* Text of the last error on this context ("" if none). Never NULL. */
+const char *sv_last_error(const sv_ctx *ctx);
+
+/* Release the context and its library buffers (not the state buffer). */
+void sv_destroy(sv_ctx *ctx);
+
+/* ------------------------------------------------------------------ host
+ * Host-side builders, callable without a GPU, exposed for inspection and
+ * testing of the period construction.
+ */
+
+/*
+ * FP64 bond gates exp(-i tau h_b) (Eq. 5) for b = 0..L-2 (gates_out:
+ * (L-1)*32 doubles, row-major complex 4x4) and the kick exp(-i theta X)
+ * (kick_out: 8 doubles).  Either output may be NULL.  Errors: SV_EINVAL.
+ */
+int sv_host_bond_gates(int L, const sv_floquet_params *p, double *gates_out,
+                       double *kick_out);
+
+/*
+ * The period as the library applies it in plain mode: gates in application
+ * order with the kick folded into the last gate on each site.  bonds_out
+ * (int[*n_gates]) and mats_out (32 doubles per gate) may be NULL to query
+ * the count; *n_gates is in/out (capacity in, count out).  Errors: SV_EINVAL.
+ */
+int sv_host_period_gates(int L, const sv_floquet_params *p, int *n_gates,
+                         int *bonds_out, double *mats_out);
+
+/*
+ * Block-mode fusion plan for one period with blocks of n sites.
+ * *n_passes is in/out (capacity in, count out).  For pass k:
+ * window_lo[k] is the first site of its n-site window, gate_count[k] the
+ * number of two-qubit gates fused into it, and, if unitaries_out is not
+ * NULL, unitaries_out + k*2*4^n holds the fused 2^n x 2^n unitary (row-major
+ * complex, local bit j = site window_lo + j).  Errors: SV_EINVAL.
+ */
+int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
+                        int *window_lo, int *gate_count, double *unitaries_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLOQUET_SV_H */

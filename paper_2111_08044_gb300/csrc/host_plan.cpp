@@ -1,0 +1,196 @@
+// Fusion planner (host, FP64): groups the period's two-qubit gates into
+// passes over the state, each applying one fused 2^n x 2^n unitary on a
+// window of n consecutive sites.  This is the single-device form of the
+// paper's fused >= 7-qubit operators (Sec. II: contractions on index
+// groups of 2^7 to fit the matrix unit).
+//
+// Search: beam search over (gates done, current window).  A pass may take
+// every pending gate inside its window whose predecessors are done.  Moving
+// the window by more than 7 sites costs extra relabel-only passes (the
+// state layout changes through a 7-bit row index), as does returning to the
+// first window (site 0) at the end of the period, because every period
+// starts from the natural layout.
+#include <algorithm>
+#include <cstdint>
+#include <unordered_set>
+
+#include "sv_internal.h"
+
+namespace fsv {
+
+namespace {
+
+constexpr int kMaxShift = 7;
+
+struct Dag {
+  std::vector<int> bond;
+  std::vector<std::vector<int>> pred;
+};
+
+Dag make_dag(const std::vector<Gate2>& gates, int L) {
+  Dag d;
+  std::vector<int> last(L, -1);
+  for (size_t k = 0; k < gates.size(); ++k) {
+    const int b = gates[k].bond;
+    d.bond.push_back(b);
+    std::vector<int> p;
+    if (last[b] >= 0) p.push_back(last[b]);
+    if (last[b + 1] >= 0 && last[b + 1] != last[b]) p.push_back(last[b + 1]);
+    d.pred.push_back(p);
+    last[b] = last[b + 1] = (int)k;
+  }
+  return d;
+}
+
+struct State {
+  std::vector<uint64_t> done;
+  int count = 0;
+  int lo = -1;
+  std::vector<std::pair<int, std::vector<int>>> hist;  // (lo, gates)
+};
+
+inline bool test(const std::vector<uint64_t>& s, int k) { return (s[k >> 6] >> (k & 63)) & 1; }
+inline void set(std::vector<uint64_t>& s, int k) { s[k >> 6] |= 1ull << (k & 63); }
+
+std::vector<int> absorb(const Dag& d, std::vector<uint64_t>& done, int lo, int n) {
+  std::vector<int> ab;
+  for (size_t k = 0; k < d.bond.size(); ++k) {
+    if (test(done, (int)k)) continue;
+    const int b = d.bond[k];
+    if (b < lo || b + 1 >= lo + n) continue;
+    bool ready = true;
+    for (int p : d.pred[k])
+      if (!test(done, p)) {
+        ready = false;
+        break;
+      }
+    if (ready) {
+      set(done, (int)k);
+      ab.push_back((int)k);
+    }
+  }
+  return ab;
+}
+
+int shift_cost(int from, int to) {
+  const int delta = std::abs(to - from);
+  return delta <= kMaxShift ? 0 : (delta + kMaxShift - 1) / kMaxShift - 1;
+}
+
+size_t key_hash(const State& s) {
+  size_t h = (size_t)s.lo * 0x9E3779B97F4A7C15ull;
+  for (uint64_t w : s.done) h ^= w + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+}  // namespace
+
+std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n) {
+  const Dag dag = make_dag(gates, L);
+  const int ng = (int)gates.size();
+  const int words = (ng + 63) / 64;
+  const size_t beam = ng <= 200 ? 256 : 32;
+  // levels[k]: states after k passes (relabel-only passes included)
+  std::vector<std::vector<State>> levels(1);
+  State s0;
+  s0.done.assign(words, 0);
+  levels[0].push_back(s0);
+  int best_total = 1 << 30;
+  State best;
+  for (int k = 0; k < (int)levels.size() && k < best_total; ++k) {
+    std::vector<State> lv = std::move(levels[k]);
+    levels[k].clear();
+    std::sort(lv.begin(), lv.end(), [](const State& a, const State& b) {
+      if (a.count != b.count) return a.count > b.count;
+      return a.lo < b.lo;
+    });
+    std::unordered_set<size_t> seen;
+    std::vector<State> kept;
+    for (auto& s : lv) {
+      if (kept.size() >= beam) break;
+      if (seen.insert(key_hash(s)).second) kept.push_back(std::move(s));
+    }
+    for (const State& s : kept) {
+      const int lo_max = s.lo < 0 ? 0 : L - n;  // the first window starts at site 0
+      for (int lo = 0; lo <= lo_max; ++lo) {
+        State t;
+        t.done = s.done;
+        std::vector<int> ab = absorb(dag, t.done, lo, n);
+        if (ab.empty()) continue;
+        t.count = s.count + (int)ab.size();
+        t.lo = lo;
+        const int cost = 1 + (s.lo < 0 ? 0 : shift_cost(s.lo, lo));
+        t.hist = s.hist;
+        for (int e = 0; e < cost - 1; ++e) t.hist.push_back({-1, {}});  // relabel-only
+        t.hist.push_back({lo, ab});
+        const int kk = k + cost;
+        if (t.count == ng) {
+          const int total = kk + shift_cost(lo, 0);
+          if (total < best_total) {
+            best_total = total;
+            best = t;
+            for (int e = 0; e < shift_cost(lo, 0); ++e) best.hist.push_back({-1, {}});
+          }
+          continue;
+        }
+        if ((int)levels.size() <= kk) levels.resize(kk + 1);
+        levels[kk].push_back(std::move(t));
+      }
+    }
+  }
+  // Materialise passes: fused unitaries, energy flags.  A relabel-only pass
+  // keeps an identity unitary on a window that steps toward the next one.
+  std::vector<BlockPass> out;
+  const size_t dim = (size_t)1 << n;
+  std::vector<int> last_gate(L, -1);
+  for (int k = 0; k < ng; ++k) {
+    last_gate[gates[k].bond] = k;
+    last_gate[gates[k].bond + 1] = k;
+  }
+  int prev_lo = 0;
+  for (size_t h = 0; h < best.hist.size(); ++h) {
+    BlockPass p;
+    p.n = n;
+    if (best.hist[h].first >= 0) {
+      p.lo = best.hist[h].first;
+      p.gates = best.hist[h].second;
+    } else {
+      // find the next real window (or site 0 at the end) and step toward it
+      int target = 0;
+      for (size_t q = h + 1; q < best.hist.size(); ++q)
+        if (best.hist[q].first >= 0) {
+          target = best.hist[q].first;
+          break;
+        }
+      const int step = std::max(-kMaxShift, std::min(kMaxShift, target - prev_lo));
+      p.lo = prev_lo + step;
+    }
+    p.U.assign(dim * dim, cd(0.0, 0.0));
+    for (size_t e = 0; e < dim; ++e) p.U[e * dim + e] = 1.0;
+    for (int g : p.gates) {
+      // U <- G_embedded U, G on local bits (j, j+1) with r = 2 b_j + b_{j+1}
+      const int j = gates[g].bond - p.lo;
+      std::vector<cd> nu(dim * dim, cd(0.0, 0.0));
+      for (size_t row = 0; row < dim; ++row) {
+        const int rr = 2 * (int)((row >> j) & 1) + (int)((row >> (j + 1)) & 1);
+        const size_t rbase = row & ~(((size_t)3) << j);
+        for (int cc = 0; cc < 4; ++cc) {
+          const cd gv = gates[g].m[4 * rr + cc];
+          if (gv == cd(0.0, 0.0)) continue;
+          const size_t src = rbase | ((size_t)(cc >> 1) << j) | ((size_t)(cc & 1) << (j + 1));
+          for (size_t col = 0; col < dim; ++col) nu[row * dim + col] += gv * p.U[src * dim + col];
+        }
+      }
+      p.U.swap(nu);
+      for (int site : {gates[g].bond, gates[g].bond + 1})
+        if (last_gate[site] == g) p.x_sites.push_back(site);
+    }
+    std::sort(p.x_sites.begin(), p.x_sites.end());
+    prev_lo = p.lo;
+    out.push_back(std::move(p));
+  }
+  if (!out.empty()) out.back().diag = true;
+  return out;
+}
+
+}  // namespace fsv

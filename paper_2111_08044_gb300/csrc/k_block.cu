@@ -1,0 +1,342 @@
+// Block form: host construction of the pass descriptors and the CUDA-core
+// FP32 block pass.  The CUDA-core pass applies any window width n <= 7 and
+// any tile height; it serves chains too short for 128-row tensor-core tiles
+// and is the reference form the tensor-core pass is checked against.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "sv_block.h"
+#include "sv_device.cuh"
+
+namespace fsv {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kSimtThreads = 512;
+
+// position of site s while the window starts at lo (see sv_block.h)
+int pos_of(int L, int n, int lo, int s) {
+  (void)L;
+  if (s >= lo && s < lo + n) return s - lo;
+  if (s < lo) return n + s;
+  return s;
+}
+
+// site held at position p while the window starts at lo
+int site_at(int L, int n, int lo, int p) {
+  (void)L;
+  if (p < n) return lo + p;
+  if (p < n + lo) return p - n;
+  return p;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kSimtThreads) k_block_simt(float2* __restrict__ psi,
+                                                             PassArgs pa) {
+  constexpr int D = 1 << N;
+  constexpr int DP = D + 1;  // padded row stride (bank spread)
+  constexpr int CH = D < 16 ? D : 16;
+  extern __shared__ float2 tile[];
+  const int R = pa.R, rows = 1 << R, a = pa.a, L = pa.L;
+  const int nel = rows * D;
+  const int nitems = rows * (D / CH);
+  const int nbits = N + R;
+  Diag<float> dg;
+  if (pa.diag) dg.init(pa.ep, L);
+  double eacc = 0.0, nacc = 0.0;
+  for (long long t = blockIdx.x; t < pa.ntiles; t += gridDim.x) {
+    const uint64_t tlo = (uint64_t)t & ((1ull << (a - N)) - 1);
+    const uint64_t thi = (uint64_t)t >> (a - N);
+    const uint64_t base = (tlo << N) | (thi << (a + R));
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int r = e >> N, c = e & (D - 1);
+      tile[r * DP + c] = psi[base + ((uint64_t)r << a) + c];
+    }
+    __syncthreads();
+    float2 acc[2][CH];
+    int rr[2], cb[2];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int item = threadIdx.x + it * blockDim.x;
+      rr[it] = item % rows;
+      cb[it] = item / rows;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) acc[it][j] = make_float2(0.f, 0.f);
+      if (item < nitems) {
+        for (int k = 0; k < D; ++k) {
+          const float2 v = tile[rr[it] * DP + k];
+#pragma unroll
+          for (int j = 0; j < CH; ++j)
+            acc[it][j] = cmac(acc[it][j], __ldg(&pa.U[(cb[it] * CH + j) * D + k]), v);
+        }
+      }
+    }
+    __syncthreads();
+    // write the result at its place in the next window's layout
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const int item = threadIdx.x + it * blockDim.x;
+      if (item >= nitems) continue;
+#pragma unroll
+      for (int j = 0; j < CH; ++j) {
+        const int y = (rr[it] << N) | (cb[it] * CH + j);
+        int yo = 0;
+        for (int q = 0; q < nbits; ++q) yo |= ((y >> q) & 1) << pa.sigma[q];
+        tile[(yo >> N) * DP + (yo & (D - 1))] = acc[it][j];
+      }
+    }
+    __syncthreads();
+    float es = 0.f, ns = 0.f;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int r = e >> N, c = e & (D - 1);
+      const float2 v = tile[r * DP + c];
+      const uint64_t x = base + ((uint64_t)r << a) + c;
+      psi[x] = v;
+      if (pa.x_mask) {
+        for (int j = 0; j < N; ++j)
+          if ((pa.x_mask >> j) & 1) {
+            const int yf = e ^ (1 << pa.sigma[j]);
+            es += pa.cx[j] * cdotre(v, tile[(yf >> N) * DP + (yf & (D - 1))]);
+          }
+      }
+      if (pa.diag) {
+        const float p = cabs2(v);
+        ns += p;
+        es += p * dg(x);
+      }
+    }
+    eacc += (double)es;
+    nacc += (double)ns;
+    __syncthreads();
+  }
+  if (pa.partial) block_store_pair(eacc, nacc, pa.partial);
+}
+
+template <int N>
+cudaError_t prepare_simt_n() {
+  return cudaFuncSetAttribute(k_block_simt<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float2) * 128 * ((1 << N) + 1)));
+}
+
+template <int N>
+cudaError_t launch_simt_n(const PassArgs& pa, void* psi, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * ((size_t)1 << pa.R) * ((1 << N) + 1);
+  k_block_simt<N><<<grid, kSimtThreads, smem, s>>>(static_cast<float2*>(psi), pa);
+  return cudaGetLastError();
+}
+
+// Opt the CUDA-core pass for width n into its shared-memory size (called at
+// build time, outside any stream capture).
+cudaError_t prepare_simt(int n) {
+  switch (n) {
+    case 2: return prepare_simt_n<2>();
+    case 3: return prepare_simt_n<3>();
+    case 4: return prepare_simt_n<4>();
+    case 5: return prepare_simt_n<5>();
+    case 6: return prepare_simt_n<6>();
+    case 7: return prepare_simt_n<7>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStream_t s) {
+  switch (pa.n) {
+    case 2: return launch_simt_n<2>(pa, psi, grid, s);
+    case 3: return launch_simt_n<3>(pa, psi, grid, s);
+    case 4: return launch_simt_n<4>(pa, psi, grid, s);
+    case 5: return launch_simt_n<5>(pa, psi, grid, s);
+    case 6: return launch_simt_n<6>(pa, psi, grid, s);
+    case 7: return launch_simt_n<7>(pa, psi, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
+                int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg) {
+  *out = nullptr;
+  if (split != SV_SPLIT_TF32X3 && split != SV_SPLIT_FP32) {
+    *msg = "unknown split";
+    return SV_EINVAL;
+  }
+  BlockPlan* bp = new BlockPlan();
+  bp->L = L;
+  bp->n = n;
+  bp->R = std::min(7, L - n);
+  bp->split = split;
+  bp->cfg = cfg;
+  bp->passes = fusion_plan(L, gates, n);
+  const int P = (int)bp->passes.size();
+  const int R = bp->R;
+  bp->tensor_cores = split == SV_SPLIT_TF32X3 && block_tc_supported(L, n);
+  const long long ntiles = 1ll << (L - n - R);
+  const int per_sm = bp->tensor_cores ? 1 : 2;
+  bp->grid = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)cfg.num_sms * per_sm));
+  bp->maxb = bp->grid;
+  auto fail = [&](const std::string& m) {
+    *msg = m;
+    block_free(bp);
+    return SV_EINVAL;
+  };
+  int slot = 0;
+  for (int k = 0; k < P; ++k) {
+    const BlockPass& ps = bp->passes[k];
+    const int lo = ps.lo;
+    const int lo_next = bp->passes[(k + 1) % P].lo;
+    const int lo_min = std::min(lo, lo_next);
+    const int delta = std::abs(lo_next - lo);
+    if (delta > R) return fail("window moves by more than the tile's row bits");
+    int a = (R == L - n) ? n : std::max(n, std::min(n + lo_min, L - R));
+    if (!(a <= n + lo_min && n + lo_min + delta <= a + R)) return fail("row bits miss moved sites");
+    PassArgs pa;
+    pa.L = L;
+    pa.n = n;
+    pa.R = R;
+    pa.a = a;
+    pa.lo = lo;
+    pa.ntiles = ntiles;
+    for (int q = 0; q < n + R; ++q) {
+      const int p = q < n ? q : a + q - n;
+      const int s = site_at(L, n, lo, p);
+      const int po = pos_of(L, n, lo_next, s);
+      int qo;
+      if (po < n) qo = po;
+      else if (po >= a && po < a + R) qo = po - a + n;
+      else return fail("site leaves the tile");
+      pa.sigma[q] = (int8_t)qo;
+    }
+    for (int p = 0; p < L; ++p) {
+      const bool in_tile = p < n || (p >= a && p < a + R);
+      if (!in_tile && site_at(L, n, lo, p) != site_at(L, n, lo_next, p))
+        return fail("layout change outside the tile");
+    }
+    for (int s : ps.x_sites) {
+      const int j = s - lo;
+      if (j < 0 || j >= n) return fail("measured site outside window");
+      pa.x_mask |= 1u << j;
+      pa.cx[j] = (float)obs.cx[s];
+    }
+    pa.diag = ps.diag ? 1 : 0;
+    if (pa.diag) {
+      if (lo_next != 0) return fail("last pass must hand back the natural layout");
+      pa.ep.flags = EPI_DIAG;
+      pa.ep.J = obs.J;
+      pa.ep.cz_first = obs.cz[0];
+      pa.ep.cz_last = obs.cz[L - 1];
+      pa.ep.cz_bulk = L >= 3 ? obs.cz[1] : 0.0;
+    }
+    if (pa.x_mask || pa.diag) pa.slot = slot++;
+    bp->args.push_back(pa);
+  }
+  bp->nslots = slot;
+  // device buffers
+  const size_t dim = (size_t)1 << n;
+  std::vector<float2> hu((size_t)P * dim * dim);
+  for (int k = 0; k < P; ++k)
+    for (size_t e = 0; e < dim * dim; ++e)
+      hu[k * dim * dim + e] = make_float2((float)bp->passes[k].U[e].real(),
+                                          (float)bp->passes[k].U[e].imag());
+  if (cudaMalloc(&bp->d_U, sizeof(float2) * hu.size()) != cudaSuccess ||
+      cudaMemcpy(bp->d_U, hu.data(), sizeof(float2) * hu.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    *msg = "unitary upload failed";
+    block_free(bp);
+    return SV_ENOMEM;
+  }
+  if (bp->tensor_cores) {
+    bp->w_bytes_per_pass = block_tc_w_bytes(n);
+    std::vector<uint32_t> hw;
+    std::vector<uint32_t> all;
+    for (int k = 0; k < P; ++k) {
+      block_tc_pack_w(n, bp->passes[k].U, hw);
+      all.insert(all.end(), hw.begin(), hw.end());
+    }
+    if (cudaMalloc(&bp->d_W, all.size() * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemcpy(bp->d_W, all.data(), all.size() * sizeof(uint32_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      *msg = "operand upload failed";
+      block_free(bp);
+      return SV_ENOMEM;
+    }
+  }
+  const size_t pbytes = sizeof(double) * 2 * std::max(1, bp->nslots) * (size_t)bp->maxb;
+  if (cudaMalloc(&bp->d_partials, pbytes) != cudaSuccess ||
+      cudaMemset(bp->d_partials, 0, pbytes) != cudaSuccess) {
+    cudaGetLastError();
+    *msg = "partials allocation failed";
+    block_free(bp);
+    return SV_ENOMEM;
+  }
+  for (int k = 0; k < P; ++k) {
+    PassArgs& pa = bp->args[k];
+    pa.U = bp->d_U + (size_t)k * dim * dim;
+    if (bp->d_W)
+      pa.W = static_cast<const char*>(bp->d_W) + (size_t)k * bp->w_bytes_per_pass;
+    if (pa.slot >= 0) pa.partial = bp->d_partials + 2 * (size_t)pa.slot * bp->maxb;
+  }
+  if (prepare_simt(n) != cudaSuccess) {
+    cudaGetLastError();
+    *msg = "shared-memory opt-in failed";
+    block_free(bp);
+    return SV_ECUDA;
+  }
+  *out = bp;
+  return SV_OK;
+}
+
+void block_info(const BlockPlan* bp, int* passes, int* launches) {
+  if (passes) *passes = (int)bp->passes.size();
+  if (launches) *launches = (int)bp->passes.size() + 1;
+}
+
+size_t block_upload_bytes(const BlockPlan* bp) {
+  const size_t P = bp->passes.size();
+  return P * sizeof(float2) * ((size_t)1 << (2 * bp->n)) + P * bp->w_bytes_per_pass;
+}
+
+cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
+                                 int ring_len, cudaStream_t s) {
+  for (const PassArgs& pa : bp->args) {
+    cudaError_t e = bp->tensor_cores ? launch_block_tc(pa, psi, bp->grid, s)
+                                     : launch_block_simt(pa, psi, bp->grid, s);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_period_reduce(bp->d_partials, (long long)bp->nslots * bp->maxb, bp->L, ring,
+                              ring_len, counter, 1, s);
+}
+
+cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* counter,
+                                        double* ring, int ring_len, cudaStream_t s,
+                                        cudaEvent_t* ev) {
+  int k = 0;
+  for (const PassArgs& pa : bp->args) {
+    cudaError_t e = cudaEventRecord(ev[k++], s);
+    if (e != cudaSuccess) return e;
+    e = bp->tensor_cores ? launch_block_tc(pa, psi, bp->grid, s)
+                         : launch_block_simt(pa, psi, bp->grid, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaEventRecord(ev[k++], s);
+  if (e != cudaSuccess) return e;
+  e = launch_period_reduce(bp->d_partials, (long long)bp->nslots * bp->maxb, bp->L, ring,
+                           ring_len, counter, 1, s);
+  if (e != cudaSuccess) return e;
+  return cudaEventRecord(ev[k], s);
+}
+
+void block_free(BlockPlan* bp) {
+  if (!bp) return;
+  cudaFree(bp->d_U);
+  cudaFree(bp->d_W);
+  cudaFree(bp->d_partials);
+  delete bp;
+}
+
+}  // namespace fsv

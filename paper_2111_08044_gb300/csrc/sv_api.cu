@@ -1,0 +1,753 @@
+// C ABI of the simulator (include/floquet_sv.h): context, state attachment,
+// period construction, evolution under a captured CUDA graph, energy
+// readback.  All device work goes to the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sv_block.h"
+#include "sv_internal.h"
+#include "sv_kernels.h"
+
+using fsv::cd;
+
+namespace {
+constexpr int kRing = 1024;  // energy ring (periods between host readbacks)
+}
+
+struct sv_ctx {
+  int device = 0;
+  int precision = SV_C64;
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // internal stream used only for capture
+  fsv::LaunchCfg cfg;
+
+  void* state = nullptr;
+  size_t state_bytes = 0;
+  int L = 0;
+  bool inited = false;
+  bool built = false;
+  int64_t counter = 0;  // host mirror of the device period counter
+
+  sv_floquet_params params{};
+  std::vector<double> theta_p, hx_p;
+  int64_t n_period_params = 0;
+  std::vector<fsv::Gate2> gates;  // period 0 (the layout of every period)
+  fsv::Observable obs;
+
+  // device buffers owned by the library
+  void* d_gates = nullptr;  // [n_tables][n_gates][16] complex
+  size_t d_gates_bytes = 0;
+  void* d_ident = nullptr;  // identity 4x4 (measurement passes)
+  double* d_spinors = nullptr;
+  double* d_part_evolve = nullptr;
+  double* d_part_meas = nullptr;
+  int part_slots_evolve = 0, part_slots_meas = 0;
+  int maxb = 0;
+  double* d_ring = nullptr;
+  double* d_meas = nullptr;
+  long long* d_counter = nullptr;
+  fsv::BlockPlan* block = nullptr;  // block-mode plan and buffers
+
+  cudaGraphExec_t graph = nullptr;
+
+  int launches_per_period = 0;
+  int passes_per_period = 0;
+  size_t build_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(sv_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(sv_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, SV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SV_CUDA(call, what)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+size_t amp_bytes(int precision) { return precision == SV_C128 ? 16 : 8; }
+
+void drop_graph(sv_ctx* ctx) {
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+}
+
+void free_build(sv_ctx* ctx) {
+  drop_graph(ctx);
+  cudaFree(ctx->d_gates);
+  ctx->d_gates = nullptr;
+  ctx->d_gates_bytes = 0;
+  cudaFree(ctx->d_part_evolve);
+  ctx->d_part_evolve = nullptr;
+  if (ctx->block) {
+    fsv::block_free(ctx->block);
+    ctx->block = nullptr;
+  }
+  ctx->built = false;
+}
+
+fsv::EpiParams epi_for(const sv_ctx* ctx, int flags, int bond, double* partial) {
+  fsv::EpiParams ep;
+  ep.flags = flags;
+  const fsv::Observable& o = ctx->obs;
+  if (flags & fsv::EPI_X_HI) ep.cx_hi = o.cx[bond];
+  if (flags & fsv::EPI_X_LO) ep.cx_lo = o.cx[bond + 1];
+  if (flags & fsv::EPI_DIAG) {
+    ep.J = o.J;
+    ep.cz_first = o.cz[0];
+    ep.cz_last = o.cz[o.L - 1];
+    ep.cz_bulk = o.L >= 3 ? o.cz[1] : 0.0;
+  }
+  ep.partial = partial;
+  return ep;
+}
+
+// Enqueue one plain-mode period on stream s.
+int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
+  const int ng = (int)ctx->gates.size();
+  const size_t cbytes = amp_bytes(ctx->precision);
+  const long long stride = ctx->n_period_params > 0 ? (long long)ng * 16 : 0;
+  int slot = 0;
+  for (int g = 0; g < ng; ++g) {
+    const fsv::Gate2& gt = ctx->gates[g];
+    double* part = gt.epi ? ctx->d_part_evolve + (size_t)slot * ctx->maxb * 2 : nullptr;
+    if (gt.epi) ++slot;
+    fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
+    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
+    SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
+                                   ctx->d_counter, ep, 1, ctx->cfg, s),
+            "plain gate launch");
+  }
+  SV_CUDA(fsv::launch_period_reduce(ctx->d_part_evolve,
+                                    (long long)ctx->part_slots_evolve * ctx->maxb, ctx->L,
+                                    ctx->d_ring, kRing, ctx->d_counter, 1, s),
+          "period reduce launch");
+  return SV_OK;
+}
+
+int enqueue_period(sv_ctx* ctx, cudaStream_t s) {
+  if (ctx->params.mode == SV_MODE_BLOCK) {
+    cudaError_t e = fsv::block_enqueue_period(ctx->block, ctx->state, ctx->d_counter,
+                                              ctx->d_ring, kRing, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "block period launch");
+    return SV_OK;
+  }
+  return enqueue_plain_period(ctx, s);
+}
+
+int ensure_graph(sv_ctx* ctx) {
+  if (ctx->graph) return SV_OK;
+  cudaGraph_t g = nullptr;
+  SV_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed),
+          "begin capture");
+  int rc = enqueue_period(ctx, ctx->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (rc != SV_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ctx->graph = nullptr;
+    return cuda_fail(ctx, e, "graph instantiate");
+  }
+  return SV_OK;
+}
+
+int check_ready(sv_ctx* ctx, bool need_built) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
+  if (!ctx->inited) return fail(ctx, SV_ESTATE, "sv_init has not been called");
+  if (need_built && !ctx->built) return fail(ctx, SV_ESTATE, "sv_build_floquet has not been called");
+  return SV_OK;
+}
+
+// Read-only measurement of <H0> and the norm of the current state.
+int measure(sv_ctx* ctx, double* e_out, double* n_out) {
+  const int L = ctx->L;
+  struct Item {
+    int bond, flags;
+  };
+  std::vector<Item> items;
+  for (int b = 0; b + 1 < L; b += 2)
+    items.push_back({b, fsv::EPI_X_HI | fsv::EPI_X_LO | (b == 0 ? fsv::EPI_DIAG : 0)});
+  if (L % 2 == 1) items.push_back({L - 2, fsv::EPI_X_LO});
+  SV_CUDA(cudaMemsetAsync(ctx->d_part_meas, 0,
+                          sizeof(double) * 2 * ctx->maxb * ctx->part_slots_meas, ctx->stream),
+          "memset partials");
+  for (size_t k = 0; k < items.size(); ++k) {
+    fsv::EpiParams ep = epi_for(ctx, items[k].flags, items[k].bond,
+                                ctx->d_part_meas + k * ctx->maxb * 2);
+    SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, L, items[k].bond,
+                                   ctx->d_ident, 0, ctx->d_counter, ep, 0, ctx->cfg,
+                                   ctx->stream),
+            "measurement launch");
+  }
+  SV_CUDA(fsv::launch_period_reduce(ctx->d_part_meas, (long long)items.size() * ctx->maxb, L,
+                                    ctx->d_meas, 1, ctx->d_counter, 0, ctx->stream),
+          "measurement reduce");
+  double h[2];
+  SV_CUDA(cudaMemcpyAsync(h, ctx->d_meas, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream),
+          "copy energy");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (e_out) *e_out = h[0];
+  if (n_out) *n_out = h[1];
+  return SV_OK;
+}
+
+// Copy ring slots of periods c0 .. c0+count-1 (count <= kRing) to the host.
+int read_ring(sv_ctx* ctx, int64_t c0, int64_t count, double* e_out, double* n_out) {
+  std::vector<double> buf(2 * (size_t)count);
+  const int64_t s0 = c0 % kRing;
+  const int64_t first = std::min<int64_t>(count, kRing - s0);
+  SV_CUDA(cudaMemcpyAsync(buf.data(), ctx->d_ring + 2 * s0, sizeof(double) * 2 * first,
+                          cudaMemcpyDeviceToHost, ctx->stream),
+          "copy ring");
+  if (first < count)
+    SV_CUDA(cudaMemcpyAsync(buf.data() + 2 * first, ctx->d_ring,
+                            sizeof(double) * 2 * (count - first), cudaMemcpyDeviceToHost,
+                            ctx->stream),
+            "copy ring");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  for (int64_t k = 0; k < count; ++k) {
+    if (e_out) e_out[k] = buf[2 * k];
+    if (n_out) n_out[k] = buf[2 * k + 1];
+  }
+  return SV_OK;
+}
+
+// One period with an event recorded before each launch and after the last.
+int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
+  if (ctx->params.mode == SV_MODE_BLOCK) {
+    cudaError_t e = fsv::block_enqueue_period_events(ctx->block, ctx->state, ctx->d_counter,
+                                                     ctx->d_ring, kRing, s, ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "block period launch");
+    return SV_OK;
+  }
+  const int ng = (int)ctx->gates.size();
+  const size_t cbytes = amp_bytes(ctx->precision);
+  const long long stride = ctx->n_period_params > 0 ? (long long)ng * 16 : 0;
+  int slot = 0;
+  for (int g = 0; g < ng; ++g) {
+    const fsv::Gate2& gt = ctx->gates[g];
+    double* part = gt.epi ? ctx->d_part_evolve + (size_t)slot * ctx->maxb * 2 : nullptr;
+    if (gt.epi) ++slot;
+    fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
+    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
+    SV_CUDA(cudaEventRecord(ev[g], s), "event record");
+    SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
+                                   ctx->d_counter, ep, 1, ctx->cfg, s),
+            "plain gate launch");
+  }
+  SV_CUDA(cudaEventRecord(ev[ng], s), "event record");
+  SV_CUDA(fsv::launch_period_reduce(ctx->d_part_evolve,
+                                    (long long)ctx->part_slots_evolve * ctx->maxb, ctx->L,
+                                    ctx->d_ring, kRing, ctx->d_counter, 1, s),
+          "period reduce launch");
+  SV_CUDA(cudaEventRecord(ev[ng + 1], s), "event record");
+  return SV_OK;
+}
+
+template <typename T>
+void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<T>& out, size_t at) {
+  for (size_t g = 0; g < gates.size(); ++g)
+    for (int k = 0; k < 16; ++k) {
+      out[at + 16 * g + k].x = (decltype(out[0].x))gates[g].m[k].real();
+      out[at + 16 * g + k].y = (decltype(out[0].x))gates[g].m[k].imag();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sv_version(void) { return 1; }
+
+int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
+  if (!out) return SV_EINVAL;
+  *out = nullptr;
+  if (precision != SV_C64 && precision != SV_C128) return SV_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return SV_ECUDA;
+  }
+  sv_ctx* ctx = new (std::nothrow) sv_ctx();
+  if (!ctx) return SV_ENOMEM;
+  ctx->device = device;
+  ctx->precision = precision;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard dg(device);
+  if (!dg.ok) {
+    delete ctx;
+    return SV_ECUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+    delete ctx;
+    return SV_ECUDA;
+  }
+  ctx->cfg.num_sms = prop.multiProcessorCount;
+  ctx->maxb = ctx->cfg.num_sms * 4;
+  ctx->part_slots_meas = 18;  // ceil(34 / 2) + 1 measurement passes at most
+  bool ok = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_spinors, sizeof(double) * 4 * 40) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_ring, sizeof(double) * 2 * kRing) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_meas, sizeof(double) * 2) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_counter, sizeof(long long)) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_ident, 16 * 16) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_part_meas, sizeof(double) * 2 * ctx->maxb *
+                                               ctx->part_slots_meas) == cudaSuccess;
+  if (ok) {
+    if (precision == SV_C128) {
+      double2 id[16] = {};
+      for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0;
+      ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
+    } else {
+      float2 id[16] = {};
+      for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0f;
+      ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    ok = ok && cudaMemset(ctx->d_counter, 0, sizeof(long long)) == cudaSuccess;
+    ok = ok && cudaMemset(ctx->d_ring, 0, sizeof(double) * 2 * kRing) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    sv_destroy(ctx);
+    return SV_ENOMEM;
+  }
+  *out = ctx;
+  return SV_OK;
+}
+
+int sv_attach_state(sv_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (!ctx) return SV_EINVAL;
+  if (!dev_ptr) return fail(ctx, SV_EINVAL, "null state pointer");
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0)
+    return fail(ctx, SV_EINVAL, "state buffer must be 256-byte aligned");
+  if (ctx->state != dev_ptr) drop_graph(ctx);
+  ctx->state = dev_ptr;
+  ctx->state_bytes = bytes;
+  if (ctx->inited && bytes < (amp_bytes(ctx->precision) << ctx->L)) {
+    ctx->inited = false;
+  }
+  return SV_OK;
+}
+
+int sv_init(sv_ctx* ctx, int L, const double* product_state) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
+  const int lmax = ctx->precision == SV_C128 ? 33 : 34;
+  if (L < 2 || L > lmax) return fail(ctx, SV_EINVAL, "L=%d out of range 2..%d", L, lmax);
+  if (!product_state) return fail(ctx, SV_EINVAL, "null product_state");
+  if (ctx->state_bytes < (amp_bytes(ctx->precision) << L))
+    return fail(ctx, SV_EINVAL, "state buffer of %zu bytes is too small for L=%d",
+                ctx->state_bytes, L);
+  std::vector<double> sp(4 * (size_t)L);
+  for (int i = 0; i < L; ++i) {
+    const double* s = product_state + 4 * i;
+    double n2 = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + s[3] * s[3];
+    if (!(n2 > 0.0) || !std::isfinite(n2))
+      return fail(ctx, SV_EINVAL, "site %d spinor has zero or non-finite norm", i);
+    double inv = 1.0 / std::sqrt(n2);
+    for (int k = 0; k < 4; ++k) sp[4 * i + k] = s[k] * inv;
+  }
+  DeviceGuard dg(ctx->device);
+  if (L != ctx->L) free_build(ctx);
+  SV_CUDA(cudaMemcpyAsync(ctx->d_spinors, sp.data(), sizeof(double) * sp.size(),
+                          cudaMemcpyHostToDevice, ctx->stream),
+          "upload spinors");
+  SV_CUDA(fsv::launch_product_state(ctx->precision, ctx->state, L, ctx->d_spinors, ctx->cfg,
+                                    ctx->stream),
+          "product state launch");
+  SV_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(long long), ctx->stream), "reset counter");
+  // the spinor buffer is read by the launch above before any later upload
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  ctx->L = L;
+  ctx->inited = true;
+  ctx->counter = 0;
+  return SV_OK;
+}
+
+int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
+  if (!ctx) return SV_EINVAL;
+  if (!p) return fail(ctx, SV_EINVAL, "null params");
+  if (!ctx->inited) return fail(ctx, SV_ESTATE, "sv_init must come before sv_build_floquet");
+  std::string why;
+  if (!fsv::params_valid(ctx->L, *p, &why)) return fail(ctx, SV_EINVAL, "%s", why.c_str());
+  if (p->mode == SV_MODE_BLOCK && p->n_period_params > 0)
+    return fail(ctx, SV_EUNSUPPORTED, "per-period parameters need SV_MODE_PLAIN");
+  if (p->mode == SV_MODE_BLOCK && ctx->precision != SV_C64)
+    return fail(ctx, SV_EUNSUPPORTED, "block mode needs SV_C64");
+  DeviceGuard dg(ctx->device);
+  free_build(ctx);
+  ctx->params = *p;
+  ctx->n_period_params = p->n_period_params;
+  ctx->theta_p.clear();
+  ctx->hx_p.clear();
+  if (p->n_period_params > 0) {
+    ctx->theta_p.assign(p->n_period_params, p->theta);
+    ctx->hx_p.assign(p->n_period_params, p->hx);
+    for (int64_t k = 0; k < p->n_period_params; ++k) {
+      if (p->theta_p) ctx->theta_p[k] = p->theta_p[k];
+      if (p->hx_p) ctx->hx_p[k] = p->hx_p[k];
+      if (!std::isfinite(ctx->theta_p[k]) || !std::isfinite(ctx->hx_p[k]))
+        return fail(ctx, SV_EINVAL, "non-finite per-period parameter at %lld", (long long)k);
+    }
+  }
+  ctx->params.theta_p = nullptr;
+  ctx->params.hx_p = nullptr;
+  ctx->obs = fsv::observable(ctx->L, *p);
+  const double th0 = p->n_period_params > 0 ? ctx->theta_p[0] : p->theta;
+  const double hx0 = p->n_period_params > 0 ? ctx->hx_p[0] : p->hx;
+  ctx->gates = fsv::period_gates(ctx->L, *p, th0, hx0);
+  const int ng = (int)ctx->gates.size();
+  if (p->mode == SV_MODE_BLOCK) {
+    int n = p->block_n ? p->block_n : 6;
+    if (n < 2 || n > 7) return fail(ctx, SV_EINVAL, "block_n must be in 2..7");
+    if (n > ctx->L) n = ctx->L;
+    std::string msg;
+    int rc = fsv::block_build(ctx->L, ctx->gates, ctx->obs, n, p->split, ctx->cfg,
+                              &ctx->block, &msg);
+    if (rc != SV_OK) return fail(ctx, rc, "block build: %s", msg.c_str());
+    fsv::block_info(ctx->block, &ctx->passes_per_period, &ctx->launches_per_period);
+    ctx->build_bytes = fsv::block_upload_bytes(ctx->block);
+  } else {
+    const int64_t ntab = p->n_period_params > 0 ? p->n_period_params : 1;
+    const size_t cb = amp_bytes(ctx->precision);
+    ctx->d_gates_bytes = (size_t)ntab * ng * 16 * cb;
+    if (cudaMalloc(&ctx->d_gates, ctx->d_gates_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->d_gates = nullptr;
+      return fail(ctx, SV_ENOMEM, "gate table allocation failed");
+    }
+    int slots = 0;
+    for (auto& g : ctx->gates) slots += g.epi ? 1 : 0;
+    ctx->part_slots_evolve = slots;
+    size_t pbytes = sizeof(double) * 2 * (size_t)ctx->maxb * slots;
+    if (cudaMalloc(&ctx->d_part_evolve, pbytes) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->d_part_evolve = nullptr;
+      return fail(ctx, SV_ENOMEM, "partials allocation failed");
+    }
+    SV_CUDA(cudaMemsetAsync(ctx->d_part_evolve, 0, pbytes, ctx->stream), "memset partials");
+    if (ctx->precision == SV_C128) {
+      std::vector<double2> tab((size_t)ntab * ng * 16);
+      for (int64_t k = 0; k < ntab; ++k) {
+        auto gk = k == 0 ? ctx->gates
+                         : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
+        upload_gates(gk, tab, (size_t)k * ng * 16);
+      }
+      SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
+                              cudaMemcpyHostToDevice, ctx->stream),
+              "upload gates");
+      SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+    } else {
+      std::vector<float2> tab((size_t)ntab * ng * 16);
+      for (int64_t k = 0; k < ntab; ++k) {
+        auto gk = k == 0 ? ctx->gates
+                         : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
+        upload_gates(gk, tab, (size_t)k * ng * 16);
+      }
+      SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
+                              cudaMemcpyHostToDevice, ctx->stream),
+              "upload gates");
+      SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+    }
+    ctx->passes_per_period = ng;
+    ctx->launches_per_period = ng + 1;
+    ctx->build_bytes = ctx->d_gates_bytes;
+  }
+  ctx->built = true;
+  return SV_OK;
+}
+
+int sv_evolve(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (periods < 0) return fail(ctx, SV_EINVAL, "periods must be >= 0");
+  if (ctx->n_period_params > 0 && ctx->counter + periods > ctx->n_period_params)
+    return fail(ctx, SV_EINVAL, "per-period parameters cover %lld periods, asked up to %lld",
+                (long long)ctx->n_period_params, (long long)(ctx->counter + periods));
+  DeviceGuard dg(ctx->device);
+  rc = ensure_graph(ctx);
+  if (rc) return rc;
+  const int renorm = ctx->params.renorm_every;
+  int64_t done = 0;
+  while (done < periods) {
+    const int64_t chunk = std::min<int64_t>(periods - done, kRing);
+    const int64_t c0 = ctx->counter;
+    for (int64_t k = 0; k < chunk; ++k) {
+      SV_CUDA(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
+      ++ctx->counter;
+      if (renorm > 0 && ctx->counter % renorm == 0)
+        SV_CUDA(fsv::launch_renormalize(ctx->precision, ctx->state, ctx->L, ctx->d_ring, kRing,
+                                        ctx->d_counter, ctx->cfg, ctx->stream),
+                "renormalize launch");
+    }
+    if (energy_out || norm_out) {
+      rc = read_ring(ctx, c0, chunk, energy_out ? energy_out + done : nullptr,
+                     norm_out ? norm_out + done : nullptr);
+      if (rc) return rc;
+    }
+    done += chunk;
+  }
+  if (!energy_out && !norm_out) SV_CUDA(cudaGetLastError(), "evolve");
+  return SV_OK;
+}
+
+int sv_evolve_profiled(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out,
+                       double* pass_ms) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (periods < 0) return fail(ctx, SV_EINVAL, "periods must be >= 0");
+  if (periods > kRing) return fail(ctx, SV_EINVAL, "at most %d periods per profiled call", kRing);
+  if (ctx->n_period_params > 0 && ctx->counter + periods > ctx->n_period_params)
+    return fail(ctx, SV_EINVAL, "per-period parameters exhausted");
+  DeviceGuard dg(ctx->device);
+  const int nl = ctx->launches_per_period;
+  std::vector<cudaEvent_t> ev(nl + 1, nullptr);
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return fail(ctx, SV_ECUDA, "event create failed");
+    }
+  const int64_t c0 = ctx->counter;
+  rc = SV_OK;
+  for (int64_t p = 0; p < periods && rc == SV_OK; ++p) {
+    rc = enqueue_period_profiled(ctx, ctx->stream, ev.data());
+    if (rc) break;
+    ++ctx->counter;
+    if (ctx->params.renorm_every > 0 && ctx->counter % ctx->params.renorm_every == 0) {
+      cudaError_t e = fsv::launch_renormalize(ctx->precision, ctx->state, ctx->L, ctx->d_ring,
+                                              kRing, ctx->d_counter, ctx->cfg, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "renormalize launch");
+    }
+    if (rc == SV_OK) {
+      cudaError_t e = cudaEventSynchronize(ev[nl]);
+      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "event synchronize");
+    }
+    for (int k = 0; k < nl && rc == SV_OK && pass_ms; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) pass_ms[k] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  if (energy_out || norm_out) return read_ring(ctx, c0, periods, energy_out, norm_out);
+  return SV_OK;
+}
+
+int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  DeviceGuard dg(ctx->device);
+  return measure(ctx, energy_density, norm2);
+}
+
+int sv_renormalize(sv_ctx* ctx, double* norm2_before) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  DeviceGuard dg(ctx->device);
+  double n2 = 0.0;
+  rc = measure(ctx, nullptr, &n2);
+  if (rc) return rc;
+  // place the norm where the scale pass reads it (ring slot counter - 1)
+  const int64_t slot = ((ctx->counter - 1) % kRing + kRing) % kRing;
+  SV_CUDA(cudaMemcpyAsync(ctx->d_ring + 2 * slot + 1, &n2, sizeof(double),
+                          cudaMemcpyHostToDevice, ctx->stream),
+          "upload norm");
+  SV_CUDA(fsv::launch_renormalize(ctx->precision, ctx->state, ctx->L, ctx->d_ring, kRing,
+                                  ctx->d_counter, ctx->cfg, ctx->stream),
+          "renormalize launch");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  if (norm2_before) *norm2_before = n2;
+  return SV_OK;
+}
+
+int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_density) {
+  (void)grad_theta;
+  (void)grad_hx;
+  (void)energy_density;
+  if (!ctx) return SV_EINVAL;
+  return fail(ctx, SV_EUNSUPPORTED, "adjoint not built yet");
+}
+
+int sv_get_state(sv_ctx* ctx, void* host_dst, size_t bytes) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  const size_t need = amp_bytes(ctx->precision) << ctx->L;
+  if (!host_dst || bytes < need) return fail(ctx, SV_EINVAL, "host buffer too small");
+  DeviceGuard dg(ctx->device);
+  SV_CUDA(cudaMemcpyAsync(host_dst, ctx->state, need, cudaMemcpyDeviceToHost, ctx->stream),
+          "copy state");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return SV_OK;
+}
+
+int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  const size_t need = amp_bytes(ctx->precision) << ctx->L;
+  if (!host_src || bytes < need) return fail(ctx, SV_EINVAL, "host buffer too small");
+  if (period < 0) return fail(ctx, SV_EINVAL, "period must be >= 0");
+  DeviceGuard dg(ctx->device);
+  long long c = period;
+  SV_CUDA(cudaMemcpyAsync(ctx->state, host_src, need, cudaMemcpyHostToDevice, ctx->stream),
+          "copy state");
+  SV_CUDA(cudaMemcpyAsync(ctx->d_counter, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream),
+          "set counter");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  ctx->counter = period;
+  return SV_OK;
+}
+
+int64_t sv_period_counter(const sv_ctx* ctx) { return ctx ? ctx->counter : -1; }
+
+int sv_pass_info(const sv_ctx* ctx, int* passes_per_period, int* gates_per_period,
+                 int* launches_per_period) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->built) return SV_ESTATE;
+  if (passes_per_period) *passes_per_period = ctx->passes_per_period;
+  if (gates_per_period) *gates_per_period = (int)ctx->gates.size();
+  if (launches_per_period) *launches_per_period = ctx->launches_per_period;
+  return SV_OK;
+}
+
+int sv_build_bytes(const sv_ctx* ctx, size_t* h2d_bytes) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->built) return SV_ESTATE;
+  if (h2d_bytes) *h2d_bytes = ctx->build_bytes;
+  return SV_OK;
+}
+
+const char* sv_last_error(const sv_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void sv_destroy(sv_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard dg(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_build(ctx);
+  cudaFree(ctx->d_ident);
+  cudaFree(ctx->d_spinors);
+  cudaFree(ctx->d_part_meas);
+  cudaFree(ctx->d_ring);
+  cudaFree(ctx->d_meas);
+  cudaFree(ctx->d_counter);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
+// ------------------------------------------------------------------- host
+
+int sv_host_bond_gates(int L, const sv_floquet_params* p, double* gates_out,
+                       double* kick_out) {
+  if (!p) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  const double tau = p->T / p->K;
+  if (gates_out)
+    for (int b = 0; b < L - 1; ++b) {
+      cd h[16], g[16];
+      fsv::bond_hamiltonian(L, b, p->J, p->hx, p->hz, p->edge_field_weight, h);
+      fsv::expm_herm4(h, tau, g);
+      for (int k = 0; k < 16; ++k) {
+        gates_out[32 * b + 2 * k] = g[k].real();
+        gates_out[32 * b + 2 * k + 1] = g[k].imag();
+      }
+    }
+  if (kick_out) {
+    cd r[4];
+    fsv::kick_matrix(p->theta, r);
+    for (int k = 0; k < 4; ++k) {
+      kick_out[2 * k] = r[k].real();
+      kick_out[2 * k + 1] = r[k].imag();
+    }
+  }
+  return SV_OK;
+}
+
+int sv_host_period_gates(int L, const sv_floquet_params* p, int* n_gates, int* bonds_out,
+                         double* mats_out) {
+  if (!p || !n_gates) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
+  const int cap = *n_gates;
+  *n_gates = (int)gates.size();
+  if (!bonds_out && !mats_out) return SV_OK;
+  if (cap < (int)gates.size()) return SV_EINVAL;
+  for (size_t g = 0; g < gates.size(); ++g) {
+    if (bonds_out) bonds_out[g] = gates[g].bond;
+    if (mats_out)
+      for (int k = 0; k < 16; ++k) {
+        mats_out[32 * g + 2 * k] = gates[g].m[k].real();
+        mats_out[32 * g + 2 * k + 1] = gates[g].m[k].imag();
+      }
+  }
+  return SV_OK;
+}
+
+int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
+                        int* window_lo, int* gate_count, double* unitaries_out) {
+  if (!p || !n_passes) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  if (n < 2 || n > 7 || n > L) return SV_EINVAL;
+  auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
+  auto plan = fsv::fusion_plan(L, gates, n);
+  const int cap = *n_passes;
+  *n_passes = (int)plan.size();
+  if (!window_lo && !gate_count && !unitaries_out) return SV_OK;
+  if (cap < (int)plan.size()) return SV_EINVAL;
+  const size_t dim = (size_t)1 << n;
+  for (size_t k = 0; k < plan.size(); ++k) {
+    if (window_lo) window_lo[k] = plan[k].lo;
+    if (gate_count) gate_count[k] = (int)plan[k].gates.size();
+    if (unitaries_out)
+      for (size_t e = 0; e < dim * dim; ++e) {
+        unitaries_out[k * 2 * dim * dim + 2 * e] = plan[k].U[e].real();
+        unitaries_out[k * 2 * dim * dim + 2 * e + 1] = plan[k].U[e].imag();
+      }
+  }
+  return SV_OK;
+}
+
+}  // extern "C"

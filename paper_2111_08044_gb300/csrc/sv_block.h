@@ -1,0 +1,81 @@
+// Block form: fused n-site unitaries applied one pass per block, with the
+// qubit relabelling folded into each pass's write.  Not public.
+//
+// State layout during a period.  While the window [lo, lo+n) is active,
+// site s sits at bit position
+//     s - lo   for lo <= s < lo + n   (the window on the lowest n bits),
+//     n + s    for s < lo,
+//     s        for s >= lo + n,
+// so a window at lo = 0 is the natural layout (site i = bit i).  Moving the
+// window from lo to lo' changes only positions 0..n-1 and the |lo'-lo|
+// positions starting at n + min(lo, lo'); a pass therefore reads a tile of
+// 2^(n+R) amplitudes (n window bits plus R <= 7 contiguous row bits starting
+// at position a that cover the moved positions), multiplies each row of 2^n
+// amplitudes by the fused unitary, and writes the tile back permuted into
+// the next window's layout.  Every tile is read and written by one CTA, so
+// the pass is in place.  Each period starts and ends in the natural layout.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sv_internal.h"
+#include "sv_kernels.h"
+
+namespace fsv {
+
+struct PassArgs {
+  int L = 0, n = 0, R = 0, a = 0;
+  int lo = 0;
+  long long ntiles = 0;
+  uint32_t x_mask = 0;       // window-local bits whose <X> this pass measures
+  float cx[8] = {};          // coefficient per window-local bit
+  int diag = 0;              // measure diagonal part + norm (output is natural layout)
+  int8_t sigma[16] = {};     // output tile bit of input tile bit q
+  const float2* U = nullptr; // fused unitary, FP32, row-major 2^n x 2^n
+  const void* W = nullptr;   // tensor-core operand block of this pass
+  double* partial = nullptr; // per-CTA (energy, norm) pairs or nullptr
+  int slot = -1;             // partials slot (host bookkeeping)
+  EpiParams ep;              // diagonal coefficients
+};
+
+struct BlockPlan {
+  int L = 0, n = 0, R = 0, split = 0;
+  bool tensor_cores = false;
+  std::vector<BlockPass> passes;
+  std::vector<PassArgs> args;
+  float2* d_U = nullptr;
+  void* d_W = nullptr;
+  size_t w_bytes_per_pass = 0;
+  double* d_partials = nullptr;
+  int nslots = 0;
+  int maxb = 0;
+  int grid = 0;
+  LaunchCfg cfg;
+};
+
+int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
+                int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg);
+void block_info(const BlockPlan* bp, int* passes, int* launches);
+size_t block_upload_bytes(const BlockPlan* bp);
+cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
+                                 int ring_len, cudaStream_t s);
+// As block_enqueue_period with ev[k] recorded before launch k and
+// ev[passes + 1] after the final reduce.
+cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* counter,
+                                        double* ring, int ring_len, cudaStream_t s,
+                                        cudaEvent_t* ev);
+void block_free(BlockPlan* bp);
+
+// CUDA-core FP32 pass (any n, R); tensor-core pass (n = 6, R = 7).
+cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
+cudaError_t launch_block_tc(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
+bool block_tc_supported(int L, int n);
+// Bytes of the tensor-core operand block of one pass, and its host layout.
+size_t block_tc_w_bytes(int n);
+void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);
+
+}  // namespace fsv

@@ -1,0 +1,147 @@
+// Device helpers shared by the kernels: complex arithmetic, the diagonal
+// part of H0 in the natural layout, and deterministic block reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sv_internal.h"
+#include "sv_kernels.h"
+
+namespace fsv {
+namespace dev {
+
+template <typename R>
+struct CT;
+template <>
+struct CT<float> {
+  using C = float2;
+  using V = float4;
+  static constexpr int NV = 2;  // amplitudes per vector
+  static constexpr int LV = 1;  // log2(NV)
+};
+template <>
+struct CT<double> {
+  using C = double2;
+  using V = double2;
+  static constexpr int NV = 1;
+  static constexpr int LV = 0;
+};
+
+__device__ __forceinline__ void unpack(const float4& v, float2 a[2]) {
+  a[0] = make_float2(v.x, v.y);
+  a[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ float4 pack(const float2 a[2]) {
+  return make_float4(a[0].x, a[0].y, a[1].x, a[1].y);
+}
+__device__ __forceinline__ void unpack(const double2& v, double2 a[1]) { a[0] = v; }
+__device__ __forceinline__ double2 pack(const double2 a[1]) { return a[0]; }
+
+__device__ __forceinline__ float2 cmac(float2 acc, float2 g, float2 v) {
+  acc.x = fmaf(g.x, v.x, acc.x);
+  acc.x = fmaf(-g.y, v.y, acc.x);
+  acc.y = fmaf(g.x, v.y, acc.y);
+  acc.y = fmaf(g.y, v.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 cmac(double2 acc, double2 g, double2 v) {
+  acc.x = fma(g.x, v.x, acc.x);
+  acc.x = fma(-g.y, v.y, acc.x);
+  acc.y = fma(g.x, v.y, acc.y);
+  acc.y = fma(g.y, v.x, acc.y);
+  return acc;
+}
+template <typename C>
+__device__ __forceinline__ C czero() {
+  C z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+// Re(conj(a) b)
+template <typename C>
+__device__ __forceinline__ auto cdotre(C a, C b) -> decltype(a.x) {
+  return a.x * b.x + a.y * b.y;
+}
+template <typename C>
+__device__ __forceinline__ auto cabs2(C a) -> decltype(a.x) {
+  return a.x * a.x + a.y * a.y;
+}
+
+__device__ __forceinline__ float2 shfl_xor(float2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+__device__ __forceinline__ double2 shfl_xor(double2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// Diagonal part of H0 at basis state x (site i = bit i):
+//   J sum_b s_b s_{b+1} + sum_i cz_i s_i,  s = 1 - 2 b.
+template <typename R>
+struct Diag {
+  R J, cz_bulk, cz_first, cz_last, czsum;
+  uint64_t zzmask, bulkmask;
+  int L;
+  __device__ void init(const EpiParams& ep, int L_) {
+    L = L_;
+    J = (R)ep.J;
+    cz_bulk = (R)ep.cz_bulk;
+    cz_first = (R)ep.cz_first;
+    cz_last = (R)ep.cz_last;
+    czsum = (R)(ep.cz_bulk * (L_ - 2) + ep.cz_first + ep.cz_last);
+    zzmask = (1ull << (L_ - 1)) - 1;
+    bulkmask = ((1ull << L_) - 1) & ~1ull & ~(1ull << (L_ - 1));
+  }
+  __device__ __forceinline__ R operator()(uint64_t x) const {
+    int flips = __popcll((x ^ (x >> 1)) & zzmask);
+    int nb = __popcll(x & bulkmask);
+    R up = cz_bulk * (R)nb + cz_first * (R)(x & 1) + cz_last * (R)((x >> (L - 1)) & 1);
+    return J * (R)(L - 1 - 2 * flips) + czsum - (R)2 * up;
+  }
+};
+
+// Deterministic block sum of (e, n) written to out[2*blockIdx.x + {0,1}].
+__device__ inline void block_store_pair(double e, double n, double* out) {
+  __shared__ double se[32], sn[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    n += __shfl_xor_sync(0xffffffffu, n, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    se[w] = e;
+    sn[w] = n;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    e = l < nw ? se[l] : 0.0;
+    n = l < nw ? sn[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if (l == 0) {
+      out[2 * blockIdx.x] = e;
+      out[2 * blockIdx.x + 1] = n;
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ const C* gate_ptr(const C* base, long long stride,
+                                             const long long* counter) {
+  return stride ? base + (*counter) * stride : base;
+}
+
+
+}  // namespace dev
+}  // namespace fsv

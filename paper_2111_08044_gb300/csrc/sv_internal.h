@@ -1,0 +1,66 @@
+// Internal declarations shared by the host builders, the C ABI and the
+// kernel launchers.  Not part of the public interface.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/floquet_sv.h"
+
+namespace fsv {
+
+using cd = std::complex<double>;
+
+// Epilogue flags of a plain gate pass: which energy terms it measures once
+// its gate is applied (the gate is the last one of the period on that site,
+// or the last gate of the period).
+enum : int { EPI_X_HI = 1, EPI_X_LO = 2, EPI_DIAG = 4 };
+
+struct Gate2 {
+  int bond = 0;      // acts on sites (bond, bond + 1)
+  cd m[16];          // row-major, local index r = 2 b_bond + b_{bond+1}
+  int epi = 0;       // EPI_* flags
+};
+
+// Coefficients of the observable H0 = sum_b h_b written as
+//   H0 = sum_i cx[i] X_i + sum_i cz[i] Z_i + J sum_b Z_b Z_{b+1}.
+struct Observable {
+  int L = 0;
+  double J = 0.0;
+  std::vector<double> cx, cz;
+};
+
+// a1: bond Hamiltonian h_b (4x4, r = 2 b_i + b_{i+1}) of the driven chain
+// at field hx (the per-period drive may differ from the observable's).
+void bond_hamiltonian(int L, int b, double J, double hx, double hz, double ew,
+                      cd h[16]);
+// exp(-i tau h) of a 4x4 Hermitian matrix in FP64 (real-symmetric Jacobi
+// diagonalisation of its 8x8 real embedding).
+void expm_herm4(const cd h[16], double tau, cd g[16]);
+// Frechet derivative of exp(-i tau h) in direction dh (Daleckii-Krein
+// divided differences in the eigenbasis).
+void expm_herm4_frechet(const cd h[16], const cd dh[16], double tau, cd g[16],
+                        cd d[16]);
+// kick exp(-i theta X)
+void kick_matrix(double theta, cd r[4]);
+// a1 + a2: the period's gates in application order with the kick folded
+// into the last gate on each site and epilogue flags set.
+std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
+                                double hx);
+Observable observable(int L, const sv_floquet_params &p);
+bool params_valid(int L, const sv_floquet_params &p, std::string *why);
+
+// a3: fusion of one period into n-site block passes (host, FP64).
+struct BlockPass {
+  int lo = 0;                 // window = sites lo .. lo+n-1, local bit j = site lo+j
+  int n = 0;
+  std::vector<int> gates;     // indices into the period's gate list, in order
+  std::vector<cd> U;          // 2^n x 2^n, row-major
+  std::vector<int> x_sites;   // sites whose <X> this pass measures
+  bool diag = false;          // this pass measures the diagonal terms and norm
+};
+std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2> &gates, int n);
+
+}  // namespace fsv

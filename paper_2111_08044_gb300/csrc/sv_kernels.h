@@ -1,0 +1,56 @@
+// Launch interface of the device kernels (host side).  Not public.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fsv {
+
+// Energy terms measured by a plain gate pass, in the layout of the state
+// pass that applies the gate (site i = bit i).
+struct EpiParams {
+  int flags = 0;           // EPI_* (sv_internal.h)
+  double cx_hi = 0.0;      // coefficient of <X_i>     (site i = bond)
+  double cx_lo = 0.0;      // coefficient of <X_{i+1}>
+  double J = 0.0;          // ZZ coupling of every bond
+  double cz_bulk = 0.0;    // Z coefficient of an interior site
+  double cz_first = 0.0;   // Z coefficient of site 0
+  double cz_last = 0.0;    // Z coefficient of site L-1
+  double* partial = nullptr;  // [gridDim.x][2] (energy, norm) of this launch
+};
+
+struct LaunchCfg {
+  int num_sms = 148;
+};
+
+// Grid (blocks of 256 threads) used by the plain gate pass for this L and
+// bond; it is also the number of partial pairs the pass writes.
+int plain_gate_grid(int L, int bond, int precision, const LaunchCfg& cfg);
+
+// Apply one 4x4 gate on bond `bond` in place (store = 1) or only measure
+// (store = 0).  gate: 16 complex (float2 for C64, double2 for C128) at
+// gate_base + (*counter) * period_stride (period_stride 0: fixed gate).
+cudaError_t launch_plain_gate(int precision, void* psi, int L, int bond,
+                              const void* gate_base, long long period_stride,
+                              const long long* counter, const EpiParams& ep,
+                              int store, const LaunchCfg& cfg, cudaStream_t s);
+
+// Sum `n` (energy, norm) partial pairs in a fixed order and record
+// (energy / L, norm) at ring[(*counter) % ring_len], then ++*counter
+// (advance != 0) .
+cudaError_t launch_period_reduce(const double* partials, long long n, int L,
+                                 double* ring, int ring_len, long long* counter,
+                                 int advance, cudaStream_t s);
+
+// psi_x = prod_i s_i[b_i(x)]; spinors: device, 4*L doubles (normalised).
+cudaError_t launch_product_state(int precision, void* psi, int L,
+                                 const double* spinors, const LaunchCfg& cfg,
+                                 cudaStream_t s);
+
+// psi *= 1/sqrt(norm2), norm2 read from ring[((*counter) - 1) % ring_len].
+cudaError_t launch_renormalize(int precision, void* psi, int L, const double* ring,
+                               int ring_len, const long long* counter,
+                               const LaunchCfg& cfg, cudaStream_t s);
+
+}  // namespace fsv

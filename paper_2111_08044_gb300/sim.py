@@ -1,0 +1,167 @@
+"""User-facing wrapper: a chain state in a torch CUDA tensor driven through
+the C ABI.  Torch provides device memory and the stream; every step of the
+evolution runs in libfloquetsv's kernels."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import capi
+
+
+class FloquetSimulator:
+    """One open chain of L sites on one GPU.
+
+    >>> sim = FloquetSimulator(L=12)
+    >>> sim.init_product_state(spinors)          # (L, 4) float64
+    >>> sim.build(J=1.0, hx=0.9, hz=0.4, T=0.5, K=4, theta=0.3)
+    >>> e, n = sim.evolve(100)                   # energy density, norm per period
+    """
+
+    def __init__(self, L: int, precision: str = "c64", device: int = 0, stream=None,
+                 state=None):
+        import torch
+        self._torch = torch
+        self.L = int(L)
+        self.precision = capi.SV_C128 if precision == "c128" else capi.SV_C64
+        dtype = torch.complex128 if self.precision == capi.SV_C128 else torch.complex64
+        self.device = torch.device("cuda", device)
+        if state is None:
+            state = torch.empty(1 << self.L, dtype=dtype, device=self.device)
+        if state.dtype != dtype or not state.is_cuda or not state.is_contiguous():
+            raise ValueError("state must be a contiguous CUDA tensor of the matching dtype")
+        self.state = state
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._lib = capi.load()
+        ctx = ctypes.c_void_p()
+        capi.check(self._lib.sv_create(ctypes.byref(ctx), self.device.index or 0,
+                                       self.precision, ctypes.c_void_p(self.stream.cuda_stream)),
+                   None, "sv_create")
+        self._ctx = ctx
+        capi.check(self._lib.sv_attach_state(ctx, ctypes.c_void_p(state.data_ptr()),
+                                             state.numel() * state.element_size()),
+                   ctx, "sv_attach_state")
+        self._keep = []
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.sv_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls
+    def init_product_state(self, spinors: np.ndarray):
+        sp = np.ascontiguousarray(spinors, dtype=np.float64)
+        if sp.shape != (self.L, 4):
+            raise ValueError(f"spinors must be ({self.L}, 4)")
+        capi.check(self._lib.sv_init(self._ctx, self.L, sp.ctypes.data_as(capi._dp)),
+                   self._ctx, "sv_init")
+
+    def build(self, **kw):
+        p, keep = capi.make_params(**kw)
+        self._keep = keep
+        capi.check(self._lib.sv_build_floquet(self._ctx, ctypes.byref(p)), self._ctx,
+                   "sv_build_floquet")
+
+    def evolve(self, periods: int, record: bool = True) -> Tuple[np.ndarray, np.ndarray]:
+        e = np.zeros(max(periods, 1))
+        n = np.zeros(max(periods, 1))
+        ep = e.ctypes.data_as(capi._dp) if record else None
+        np_ = n.ctypes.data_as(capi._dp) if record else None
+        capi.check(self._lib.sv_evolve(self._ctx, int(periods), ep, np_), self._ctx,
+                   "sv_evolve")
+        return e[:periods], n[:periods]
+
+    def energy(self) -> Tuple[float, float]:
+        e = ctypes.c_double()
+        n = ctypes.c_double()
+        capi.check(self._lib.sv_expect_energy(self._ctx, ctypes.byref(e), ctypes.byref(n)),
+                   self._ctx, "sv_expect_energy")
+        return e.value, n.value
+
+    def renormalize(self) -> float:
+        n = ctypes.c_double()
+        capi.check(self._lib.sv_renormalize(self._ctx, ctypes.byref(n)), self._ctx,
+                   "sv_renormalize")
+        return n.value
+
+    def adjoint(self) -> Tuple[np.ndarray, np.ndarray, float]:
+        P = self._n_period_params()
+        gt = np.zeros(P)
+        gh = np.zeros(P)
+        e = ctypes.c_double()
+        capi.check(self._lib.sv_adjoint(self._ctx, gt.ctypes.data_as(capi._dp),
+                                        gh.ctypes.data_as(capi._dp), ctypes.byref(e)),
+                   self._ctx, "sv_adjoint")
+        return gt, gh, e.value
+
+    def _n_period_params(self) -> int:
+        sizes = [k.size for k in self._keep]
+        return max(sizes) if sizes else 0
+
+    def host_state(self) -> np.ndarray:
+        dt = np.complex128 if self.precision == capi.SV_C128 else np.complex64
+        out = np.empty(1 << self.L, dtype=dt)
+        capi.check(self._lib.sv_get_state(self._ctx, ctypes.c_void_p(out.ctypes.data),
+                                          out.nbytes), self._ctx, "sv_get_state")
+        return out
+
+    def set_host_state(self, psi: np.ndarray, period: int = 0):
+        dt = np.complex128 if self.precision == capi.SV_C128 else np.complex64
+        a = np.ascontiguousarray(psi, dtype=dt)
+        capi.check(self._lib.sv_set_state(self._ctx, ctypes.c_void_p(a.ctypes.data), a.nbytes,
+                                          int(period)), self._ctx, "sv_set_state")
+
+    @property
+    def period(self) -> int:
+        return int(self._lib.sv_period_counter(self._ctx))
+
+    def evolve_profiled(self, periods: int):
+        """(energy, norm, per-launch milliseconds summed over the periods)."""
+        p, _, nl = self.pass_info()
+        e = np.zeros(max(periods, 1))
+        n = np.zeros(max(periods, 1))
+        ms = np.zeros(nl)
+        capi.check(self._lib.sv_evolve_profiled(self._ctx, int(periods), e.ctypes.data_as(capi._dp),
+                                                n.ctypes.data_as(capi._dp),
+                                                ms.ctypes.data_as(capi._dp)),
+                   self._ctx, "sv_evolve_profiled")
+        return e[:periods], n[:periods], ms
+
+    def build_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        capi.check(self._lib.sv_build_bytes(self._ctx, ctypes.byref(b)), self._ctx,
+                   "sv_build_bytes")
+        return b.value
+
+    def pass_info(self):
+        p, g, l = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        capi.check(self._lib.sv_pass_info(self._ctx, ctypes.byref(p), ctypes.byref(g),
+                                          ctypes.byref(l)), self._ctx, "sv_pass_info")
+        return p.value, g.value, l.value
+
+
+def chain_params(cfg, **over):
+    """Keyword arguments of FloquetSimulator.build for a ChainConfig."""
+    kw = dict(J=cfg.J, hx=cfg.hx, hz=cfg.hz, T=cfg.T, theta=cfg.theta,
+              edge_field_weight=cfg.edge_field_weight, K=cfg.K, first_layer=cfg.first_layer)
+    if getattr(cfg, "theta_p", None) is not None:
+        kw["theta_p"] = cfg.theta_p
+    if getattr(cfg, "hx_p", None) is not None:
+        kw["hx_p"] = cfg.hx_p
+    kw.update(over)
+    return kw

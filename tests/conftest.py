@@ -28,3 +28,13 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def svlib():
+    """The CUDA library (built in-tree on first use; nvcc cross-compiles
+    without a GPU)."""
+    from paper_2111_08044_gb300 import build as b
+    from paper_2111_08044_gb300 import capi
+    b.build()
+    return capi.load()

@@ -1,0 +1,148 @@
+"""C-ABI host checks (no GPU): the library loads and exports the header's
+symbols, argument errors come back as status codes, and the host-side period
+construction (gates, kick folding, fusion) agrees with the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2111_08044_gb300 import capi, inputs
+from tests import dense_reference as dr
+
+
+def test_library_exports_every_header_symbol(svlib):
+    names = capi.header_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(svlib, n), n
+    assert svlib.sv_version() >= 1
+
+
+def test_create_without_device_is_an_error_code(svlib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = ctypes.c_void_p()
+    rc = svlib.sv_create(ctypes.byref(ctx), 0, capi.SV_C64, None)
+    assert rc == capi.SV_ECUDA
+    assert not ctx.value
+
+
+def test_argument_errors(svlib):
+    p, _ = capi.make_params()
+    out = np.zeros(64)
+    assert svlib.sv_host_bond_gates(1, ctypes.byref(p), out.ctypes.data_as(capi._dp), None) == capi.SV_EINVAL
+    assert svlib.sv_host_bond_gates(35, ctypes.byref(p), None, None) == capi.SV_EINVAL
+    bad, _ = capi.make_params(K=0)
+    assert svlib.sv_host_bond_gates(6, ctypes.byref(bad), None, None) == capi.SV_EINVAL
+    bad, _ = capi.make_params(first_layer=2)
+    assert svlib.sv_host_bond_gates(6, ctypes.byref(bad), None, None) == capi.SV_EINVAL
+    bad, _ = capi.make_params(hx=float("nan"))
+    assert svlib.sv_host_bond_gates(6, ctypes.byref(bad), None, None) == capi.SV_EINVAL
+    n = ctypes.c_int(0)
+    assert svlib.sv_host_fusion_plan(6, ctypes.byref(p), 8, ctypes.byref(n), None, None, None) == capi.SV_EINVAL
+    assert svlib.sv_host_fusion_plan(6, ctypes.byref(p), 1, ctypes.byref(n), None, None, None) == capi.SV_EINVAL
+    assert svlib.sv_host_period_gates(6, None, ctypes.byref(n), None, None) == capi.SV_EINVAL
+    # a null context is rejected everywhere
+    assert svlib.sv_init(None, 8, None) == capi.SV_EINVAL
+    assert svlib.sv_evolve(None, 1, None, None) == capi.SV_EINVAL
+    assert svlib.sv_expect_energy(None, None, None) == capi.SV_EINVAL
+    assert svlib.sv_period_counter(None) == -1
+
+
+def _lib_gates(svlib, L, **kw):
+    p, keep = capi.make_params(**kw)
+    g = np.zeros((L - 1, 4, 4), dtype=np.complex128)
+    k = np.zeros((2, 2), dtype=np.complex128)
+    assert svlib.sv_host_bond_gates(L, ctypes.byref(p), g.ctypes.data_as(capi._dp),
+                                    k.ctypes.data_as(capi._dp)) == 0
+    return g, k
+
+
+@pytest.mark.parametrize("L,ew", [(2, 0.5), (5, 1.0), (12, 0.5)])
+def test_bond_gates_match_oracle(svlib, L, ew):
+    kw = dict(J=1.1, hx=0.8, hz=0.35, T=0.7, K=3, theta=0.41, edge_field_weight=ew)
+    g, k = _lib_gates(svlib, L, **kw)
+    hb = orc.ising_bond_hamiltonians(L, 1.1, 0.8, 0.35, ew)
+    np.testing.assert_allclose(g, orc.bond_gates(hb, 0.7 / 3), atol=1e-13, rtol=0)
+    np.testing.assert_allclose(k, orc.kick_gates(1, 0.41)[0], atol=1e-15, rtol=0)
+
+
+def _period_gates(svlib, L, **kw):
+    p, keep = capi.make_params(**kw)
+    n = ctypes.c_int(0)
+    assert svlib.sv_host_period_gates(L, ctypes.byref(p), ctypes.byref(n), None, None) == 0
+    bonds = np.zeros(n.value, dtype=np.int32)
+    mats = np.zeros((n.value, 4, 4), dtype=np.complex128)
+    assert svlib.sv_host_period_gates(L, ctypes.byref(p), ctypes.byref(n),
+                                      bonds.ctypes.data_as(capi._ip),
+                                      mats.ctypes.data_as(capi._dp)) == 0
+    return bonds, mats
+
+
+@pytest.mark.parametrize("L,first", [(2, 0), (5, 0), (6, 1), (7, 1)])
+def test_folded_period_equals_oracle_period(svlib, L, first):
+    """Kick folding: the library's folded gate sequence multiplies out to the
+    same Floquet operator as the oracle's unfolded one."""
+    kw = dict(J=0.9, hx=1.1, hz=0.3, T=0.6, K=3, theta=0.27, first_layer=first)
+    bonds, mats = _period_gates(svlib, L, **kw)
+    assert len(bonds) == 3 * (L - 1)
+    U = np.eye(1 << L, dtype=np.complex128)
+    for b, m in zip(bonds, mats):
+        U = dr.two_site_op(L, int(b), m) @ U
+    hb = orc.ising_bond_hamiltonians(L, 0.9, 1.1, 0.3, 0.5)
+    Ud = dr.floquet_dense([dr.ising_bond_dense(L, b, 0.9, 1.1, 0.3, 0.5) for b in range(L - 1)],
+                          L, 0.2, 0.27, 3, first)
+    np.testing.assert_allclose(U, Ud, atol=1e-12, rtol=0)
+    # and against the oracle applying the same period to a random state
+    sp = inputs.random_product_spinors(L, 3)
+    psi = orc.product_state(sp)
+    orc.period(psi, orc.bond_gates(hb, 0.2), orc.kick_gates(L, 0.27), 3, first)
+    np.testing.assert_allclose(U @ orc.product_state(sp), psi, atol=1e-12, rtol=0)
+
+
+def _plan(svlib, L, n, **kw):
+    p, keep = capi.make_params(**kw)
+    cnt = ctypes.c_int(0)
+    assert svlib.sv_host_fusion_plan(L, ctypes.byref(p), n, ctypes.byref(cnt), None, None,
+                                     None) == 0
+    P = cnt.value
+    lo = np.zeros(P, dtype=np.int32)
+    gc = np.zeros(P, dtype=np.int32)
+    dim = 1 << n
+    U = np.zeros((P, dim, dim), dtype=np.complex128) if L <= 12 else None
+    assert svlib.sv_host_fusion_plan(
+        L, ctypes.byref(p), n, ctypes.byref(cnt), lo.ctypes.data_as(capi._ip),
+        gc.ctypes.data_as(capi._ip), None if U is None else U.ctypes.data_as(capi._dp)) == 0
+    return lo, gc, U
+
+
+def _window_op(L, lo, n, U):
+    """Embed an n-site unitary acting on sites lo..lo+n-1 (local bit j = site lo+j)."""
+    return np.kron(np.kron(np.eye(1 << (L - lo - n)), U), np.eye(1 << lo))
+
+
+@pytest.mark.parametrize("L,n", [(6, 3), (8, 4), (9, 5), (10, 6), (10, 7)])
+def test_fused_passes_multiply_to_the_period(svlib, L, n):
+    kw = dict(J=1.0, hx=0.9, hz=0.4, T=0.5, K=4, theta=0.3)
+    lo, gc, U = _plan(svlib, L, n, **kw)
+    assert gc.sum() == 4 * (L - 1)
+    assert lo[0] == 0
+    total = np.eye(1 << L, dtype=np.complex128)
+    for k in range(len(lo)):
+        total = _window_op(L, lo[k], n, U[k]) @ total
+    Ud = dr.floquet_dense([dr.ising_bond_dense(L, b, 1.0, 0.9, 0.4, 0.5) for b in range(L - 1)],
+                          L, 0.125, 0.3, 4, 0)
+    np.testing.assert_allclose(total, Ud, atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("L", [13, 20, 26, 30, 34])
+@pytest.mark.parametrize("n", [6, 7])
+def test_fusion_plan_shape_large_chains(svlib, L, n):
+    lo, gc, _ = _plan(svlib, L, n)
+    assert gc.sum() == 4 * (L - 1)
+    assert lo[0] == 0
+    jumps = np.abs(np.diff(np.concatenate([lo, [0]])))
+    assert jumps.max() <= 7  # every relabel fits in a 7-bit row index
+    assert len(lo) <= {6: 21, 7: 18}[n]

@@ -1,0 +1,54 @@
+"""GPU parity of the block form (fused n-site unitaries, relabel folded into
+each pass) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2111_08044_gb300 import capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_block(cfg, n, split, periods):
+    from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
+    with FloquetSimulator(cfg.L) as sim:
+        sim.init_product_state(cfg.spinors())
+        sim.build(**chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=n, split=split))
+        e, nn = sim.evolve(periods)
+        return e, nn, sim.host_state(), sim.pass_info()
+
+
+BLOCK_CASES = [(8, 3), (8, 4), (10, 5), (12, 6), (12, 7), (13, 6), (14, 5), (16, 6),
+               (17, 7)]
+
+
+@pytest.mark.parametrize("L,n", BLOCK_CASES)
+def test_simt_block_form_matches_oracle(svlib, L, n):
+    cfg = inputs.ChainConfig(L=L, periods=4, seed=60 + L)
+    psi_o, _, e_o, n_o = orc.run_chain(cfg)
+    e, nn, psi, info = _run_block(cfg, n, capi.SV_SPLIT_FP32, cfg.periods)
+    assert info[0] >= 1
+    err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
+    assert err < 1e-5, err
+    np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(nn, n_o, atol=2e-6, rtol=0)
+
+
+def test_block_small_preset_100_periods(svlib):
+    cfg = inputs.preset("small")
+    psi_o, _, e_o, _ = orc.run_chain(cfg)
+    e, nn, psi, _ = _run_block(cfg, 6, capi.SV_SPLIT_TF32X3, cfg.periods)
+    np.testing.assert_allclose(e, e_o, atol=1e-5, rtol=0)
+    ov = np.vdot(psi.astype(np.complex128), psi_o)
+    assert 1 - abs(ov) ** 2 < 1e-5
+
+
+@pytest.mark.parametrize("L", [14, 16, 20])
+def test_tensor_core_block_form_matches_oracle(svlib, L):
+    cfg = inputs.ChainConfig(L=L, periods=3, seed=80 + L)
+    psi_o, _, e_o, n_o = orc.run_chain(cfg)
+    e, nn, psi, _ = _run_block(cfg, 6, capi.SV_SPLIT_TF32X3, cfg.periods)
+    err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
+    assert err < 1e-5, err
+    np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(nn, n_o, atol=2e-6, rtol=0)

@@ -23,8 +23,9 @@
  *     where each bond gives each of its sites h/2 of the on-site fields,
  *     except that an open end site receives edge_field_weight * h from its
  *     one bond; then the kick exp(-i theta sum_i X_i).
- *   - H0 = sum_b h_b (Eq. 7).  Energies are of the unnormalised state; the
- *     squared norm is reported beside them.
+ *   - H0 = sum_b h_b (Eq. 7).  Reported energy densities are those of the
+ *     normalised state, <psi|H0|psi> / (L <psi|psi>); the squared norm, which
+ *     drifts from 1 only by rounding, is reported beside them.
  *   - Status: every call returns SV_OK (0) or a negative SV_E* code; no
  *     exception or abort crosses this boundary.  sv_last_error() gives text.
  *   - Memory: the state buffer belongs to the caller (device memory, e.g. a
@@ -128,7 +129,7 @@ int sv_build_floquet(sv_ctx *ctx, const sv_floquet_params *p);
 
 /*
  * Apply `periods` periods (Eq. 3).  After each period the energy density
- * <psi|H0|psi>/L and <psi|psi> are recorded; energy_out / norm_out (host,
+ * <psi|H0|psi>/(L <psi|psi>) and <psi|psi> are recorded; energy_out / norm_out (host,
  * length `periods`, either may be NULL) receive them.  With per-period
  * parameters the period counter must stay below n_period_params.
  * Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA.
@@ -146,7 +147,7 @@ int sv_evolve_profiled(sv_ctx *ctx, int64_t periods, double *energy_out,
                        double *norm_out, double *pass_ms);
 
 /*
- * Energy density <psi|H0|psi>/L (Eq. 10 / L) and <psi|psi> of the current
+ * Energy density <psi|H0|psi>/(L <psi|psi>) (Eq. 10 per site) and <psi|psi> of the current
  * state (host outputs; either may be NULL).  Errors: SV_ESTATE, SV_ECUDA.
  */
 int sv_expect_energy(sv_ctx *ctx, double *energy_density, double *norm2);

@@ -280,7 +280,8 @@ static void kick_gate(double theta, double *k8) {
 }
 
 /*
- * Evolve `periods` periods and record E_p / L and |psi|^2 after each one.
+ * Evolve `periods` periods and record the energy density of the normalised
+ * state, <psi|H0|psi> / (L <psi|psi>), and |psi|^2 after each one.
  *   hdrive : bond Hamiltonians that generate the gates, (L-1) 4x4 each;
  *            if per_period != 0 there are `periods` such sets back to back.
  *   theta  : kick angle, one value or one per period (per_period != 0).
@@ -311,7 +312,7 @@ int or_evolve(int L, double *psi, int64_t periods, const double *hdrive,
       double e = 0.0, n2 = 0.0;
       if (hobs) or_energy(L, psi, hobs, &e, &n2);
       else or_norm2(L, psi, &n2);
-      if (energy_density) energy_density[p] = e / L;
+      if (energy_density) energy_density[p] = hobs ? e / (L * n2) : 0.0;
       if (norm2) norm2[p] = n2;
     }
   }

@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(256) k_period_reduce(const double* __restrict_
   if (threadIdx.x == 0) {
     const long long c = *counter;
     const long long slot = c % ring_len;
-    ring[2 * slot] = se[0] / L;
+    // energy density of the normalised state: <psi|H0|psi> / (L <psi|psi>)
+    ring[2 * slot] = sn[0] > 0.0 ? se[0] / (L * sn[0]) : 0.0;
     ring[2 * slot + 1] = sn[0];
     if (advance) *counter = c + 1;
   }

@@ -37,8 +37,8 @@ cudaError_t launch_plain_gate(int precision, void* psi, int L, int bond,
                               int store, const LaunchCfg& cfg, cudaStream_t s);
 
 // Sum `n` (energy, norm) partial pairs in a fixed order and record
-// (energy / L, norm) at ring[(*counter) % ring_len], then ++*counter
-// (advance != 0) .
+// (energy / (L norm), norm) at ring[(*counter) % ring_len], then ++*counter
+// (advance != 0).
 cudaError_t launch_period_reduce(const double* partials, long long n, int L,
                                  double* ring, int ring_len, long long* counter,
                                  int advance, cudaStream_t s);

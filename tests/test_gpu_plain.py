@@ -36,6 +36,8 @@ def test_small_preset_100_periods(svlib, precision, tol):
         assert sim.period == cfg.periods
     assert abs(e0 - e0_o) < tol
     np.testing.assert_allclose(e, e_o, atol=tol, rtol=0)
+    # complex64: the norm may drift by rounding of the gates (no systematic
+    # bias is left after unitarity-aware FP32 rounding); complex128 holds it
     np.testing.assert_allclose(n, n_o, atol=tol, rtol=0)
     assert _infidelity(psi, psi_o) < tol
     np.testing.assert_allclose(psi, psi_o, atol=10 * tol, rtol=0)

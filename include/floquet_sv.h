@@ -200,6 +200,35 @@ const char *sv_last_error(const sv_ctx *ctx);
 /* Release the context and its library buffers (not the state buffer). */
 void sv_destroy(sv_ctx *ctx);
 
+/*
+ * Energy density <psi|H0|psi>/(L <psi|psi>) and squared norm of a chain
+ * state, for callers that cannot allocate device memory (for example code
+ * that runs while a stream is being captured with a memory pool it does not
+ * own, or a process whose device memory all belongs to an outside
+ * allocator).  The paper has no counterpart: it is a deployment variant of
+ * the measurement that sv_expect_energy makes.
+ *
+ *   psi_dev     device pointer to the 2^L amplitudes (complex64 or
+ *               complex128 by `precision`), natural layout; read only.
+ *   p           host parameters of H0 (J, hx, hz, edge_field_weight; the
+ *               other fields must be valid as for sv_build_floquet).
+ *   out_dev     device pointer to 2 doubles, written on `cuda_stream`:
+ *               out_dev[0] energy density, out_dev[1] <psi|psi>.
+ *   cuda_stream cudaStream_t the launches go to (NULL: legacy stream).
+ *
+ * Allocates nothing: its reduction scratch is a fixed 288 KiB device array
+ * of the library, held on every device that loads the library until the
+ * process exits; it supports L <= 34 (complex64) / 33 (complex128).  The
+ * first call on a device looks that array up on the current device, so
+ * make the first call before any stream capture.  Every call reuses the
+ * same array (zeroing it first), so calls that overlap on the GPU race: do
+ * not run two at once.  Returns without synchronising.  Errors: SV_EINVAL
+ * (null pointer, bad precision, L beyond the limit, invalid parameters),
+ * SV_ECUDA (symbol lookup or launch failed).
+ */
+int sv_energy_noalloc(const void *psi_dev, int L, int precision,
+                      const sv_floquet_params *p, double *out_dev, void *cuda_stream);
+
 /* ------------------------------------------------------------------ host
  * Host-side builders, callable without a GPU, exposed for inspection and
  * testing of the period construction.

@@ -80,7 +80,10 @@ typedef struct sv_floquet_params {
   int32_t mode;             /* SV_MODE_PLAIN or SV_MODE_BLOCK */
   int32_t block_n;          /* block width n for SV_MODE_BLOCK (2..7); 0 = default */
   int32_t split;            /* SV_SPLIT_* (block mode) */
-  int32_t renorm_every;     /* rescale psi to unit norm every this many periods; 0 = never */
+  int32_t renorm_every;     /* rescale psi to unit norm at the start of every this
+                               many-th period (folded into its first pass, using the
+                               FP64 norm measured at the end of the previous period);
+                               0 = never */
   int64_t n_period_params;  /* > 0: theta_p / hx_p give one value per period */
   const double *theta_p;    /* host, length n_period_params, or NULL */
   const double *hx_p;       /* host, length n_period_params, or NULL */
@@ -132,7 +135,9 @@ int sv_build_floquet(sv_ctx *ctx, const sv_floquet_params *p);
  * <psi|H0|psi>/(L <psi|psi>) and <psi|psi> are recorded; energy_out / norm_out (host,
  * length `periods`, either may be NULL) receive them.  With per-period
  * parameters the period counter must stay below n_period_params.
- * Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA.
+ * Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA, SV_ETIMEOUT (a tensor-core pass
+ * gave up a bounded wait; reported when the call synchronises, i.e. when
+ * energy_out or norm_out is given).
  */
 int sv_evolve(sv_ctx *ctx, int64_t periods, double *energy_out, double *norm_out);
 
@@ -189,6 +194,14 @@ int64_t sv_period_counter(const sv_ctx *ctx);
  */
 int sv_pass_info(const sv_ctx *ctx, int *passes_per_period, int *gates_per_period,
                  int *launches_per_period);
+
+/*
+ * The evolution form sv_build_floquet chose: *tensor_cores = 1 when block
+ * passes run on the tensor cores (tcgen05, n = 6 windows on chains of at
+ * least 13 sites), 0 for the CUDA-core block pass or the plain form;
+ * *block_n = window width (0 in plain mode).  Errors: SV_ESTATE.
+ */
+int sv_form_info(const sv_ctx *ctx, int *tensor_cores, int *block_n);
 
 /* Bytes the last sv_build_floquet copied host -> device (gate tables, fused
  * unitaries, tensor-core operands).  Errors: SV_ESTATE. */

@@ -83,6 +83,7 @@ SIGNATURES = {
     "sv_period_counter": ([_vp], _i64),
     "sv_pass_info": ([_vp, _ip, _ip, _ip], _i32),
     "sv_build_bytes": ([_vp, ctypes.POINTER(_sz)], _i32),
+    "sv_form_info": ([_vp, _ip, _ip], _i32),
     "sv_energy_noalloc": ([_vp, _i32, _i32, _pp, _dp, _vp], _i32),
     "sv_last_error": ([_vp], ctypes.c_char_p),
     "sv_destroy": ([_vp], None),

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kSimtThreads) k_block_simt(float2* __restrict_
   const int nbits = N + R;
   Diag<float> dg;
   if (pa.diag) dg.init(pa.ep, L);
+  const float sc = (float)renorm_scale(pa.ep.rn);
   double eacc = 0.0, nacc = 0.0;
   for (long long t = blockIdx.x; t < pa.ntiles; t += gridDim.x) {
     const uint64_t tlo = (uint64_t)t & ((1ull << (a - N)) - 1);
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kSimtThreads) k_block_simt(float2* __restrict_
         const int y = (rr[it] << N) | (cb[it] * CH + j);
         int yo = 0;
         for (int q = 0; q < nbits; ++q) yo |= ((y >> q) & 1) << pa.sigma[q];
-        tile[(yo >> N) * DP + (yo & (D - 1))] = acc[it][j];
+        tile[(yo >> N) * DP + (yo & (D - 1))] = make_float2(acc[it][j].x * sc, acc[it][j].y * sc);
       }
     }
     __syncthreads();
@@ -281,6 +282,15 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
       pa.W = static_cast<const char*>(bp->d_W) + (size_t)k * bp->w_bytes_per_pass;
     if (pa.slot >= 0) pa.partial = bp->d_partials + 2 * (size_t)pa.slot * bp->maxb;
   }
+  if (bp->tensor_cores) {
+    if (block_tc_prepare() != cudaSuccess || cudaMalloc(&bp->d_status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(bp->d_status, 0, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      *msg = "tensor-core pass set-up failed";
+      block_free(bp);
+      return SV_ECUDA;
+    }
+  }
   if (prepare_simt(n) != cudaSuccess) {
     cudaGetLastError();
     *msg = "shared-memory opt-in failed";
@@ -289,6 +299,10 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   }
   *out = bp;
   return SV_OK;
+}
+
+void block_set_renorm(BlockPlan* bp, const Renorm& rn) {
+  if (!bp->args.empty()) bp->args[0].ep.rn = rn;
 }
 
 void block_info(const BlockPlan* bp, int* passes, int* launches) {
@@ -301,11 +315,44 @@ size_t block_upload_bytes(const BlockPlan* bp) {
   return P * sizeof(float2) * ((size_t)1 << (2 * bp->n)) + P * bp->w_bytes_per_pass;
 }
 
+namespace {
+
+// TMA descriptors embed the state address: (re)build them for psi.
+cudaError_t ensure_maps(BlockPlan* bp, void* psi) {
+  if (!bp->tensor_cores || bp->maps_psi == psi) return cudaSuccess;
+  const size_t mb = block_tc_map_bytes();
+  bp->maps.assign(mb * bp->args.size(), 0);
+  for (size_t k = 0; k < bp->args.size(); ++k)
+    if (block_tc_make_map(bp->args[k], psi, bp->maps.data() + k * mb) != SV_OK)
+      return cudaErrorInvalidValue;
+  bp->maps_psi = psi;
+  return cudaSuccess;
+}
+
+cudaError_t launch_pass(BlockPlan* bp, size_t k, void* psi, cudaStream_t s) {
+  if (bp->tensor_cores)
+    return launch_block_tc(bp->args[k], bp->maps.data() + k * block_tc_map_bytes(),
+                           bp->d_status, bp->grid, s);
+  return launch_block_simt(bp->args[k], psi, bp->grid, s);
+}
+
+}  // namespace
+
+int block_status(BlockPlan* bp, cudaStream_t s) {
+  if (!bp || !bp->d_status) return 0;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, bp->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return h;
+}
+
 cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
                                  int ring_len, cudaStream_t s) {
-  for (const PassArgs& pa : bp->args) {
-    cudaError_t e = bp->tensor_cores ? launch_block_tc(pa, psi, bp->grid, s)
-                                     : launch_block_simt(pa, psi, bp->grid, s);
+  cudaError_t e = ensure_maps(bp, psi);
+  if (e != cudaSuccess) return e;
+  for (size_t k = 0; k < bp->args.size(); ++k) {
+    e = launch_pass(bp, k, psi, s);
     if (e != cudaSuccess) return e;
   }
   return launch_period_reduce(bp->d_partials, (long long)bp->nslots * bp->maxb, bp->L, ring,
@@ -315,15 +362,16 @@ cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, d
 cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* counter,
                                         double* ring, int ring_len, cudaStream_t s,
                                         cudaEvent_t* ev) {
-  int k = 0;
-  for (const PassArgs& pa : bp->args) {
-    cudaError_t e = cudaEventRecord(ev[k++], s);
+  cudaError_t e = ensure_maps(bp, psi);
+  if (e != cudaSuccess) return e;
+  size_t k = 0;
+  for (; k < bp->args.size(); ++k) {
+    e = cudaEventRecord(ev[k], s);
     if (e != cudaSuccess) return e;
-    e = bp->tensor_cores ? launch_block_tc(pa, psi, bp->grid, s)
-                         : launch_block_simt(pa, psi, bp->grid, s);
+    e = launch_pass(bp, k, psi, s);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = cudaEventRecord(ev[k++], s);
+  e = cudaEventRecord(ev[k++], s);
   if (e != cudaSuccess) return e;
   e = launch_period_reduce(bp->d_partials, (long long)bp->nslots * bp->maxb, bp->L, ring,
                            ring_len, counter, 1, s);
@@ -336,6 +384,7 @@ void block_free(BlockPlan* bp) {
   cudaFree(bp->d_U);
   cudaFree(bp->d_W);
   cudaFree(bp->d_partials);
+  cudaFree(bp->d_status);
   delete bp;
 }
 

@@ -49,9 +49,14 @@ __global__ void __launch_bounds__(kThreads) k_gate_high(
   using V = typename CT<R>::V;
   constexpr int NV = CT<R>::NV, LV = CT<R>::LV;
   const C* gp = gate_ptr(gate_base, stride, counter);
+  const R sc = (R)renorm_scale(ep.rn);
   C g[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) g[k] = gp[k];
+  for (int k = 0; k < 16; ++k) {
+    g[k] = gp[k];
+    g[k].x *= sc;
+    g[k].y *= sc;
+  }
   Diag<R> dg;
   if (ep.flags & EPI_DIAG) dg.init(ep, L);
   const R cxh = (R)ep.cx_hi, cxl = (R)ep.cx_lo;
@@ -179,7 +184,13 @@ __global__ void __launch_bounds__(kThreads) k_gate_low(
   constexpr int NV = CT<R>::NV, LV = CT<R>::LV;
   __shared__ C gs[16];
   const C* gp = gate_ptr(gate_base, stride, counter);
-  if (threadIdx.x < 16) gs[threadIdx.x] = gp[threadIdx.x];
+  if (threadIdx.x < 16) {
+    const R sc = (R)renorm_scale(ep.rn);
+    C g = gp[threadIdx.x];
+    g.x *= sc;
+    g.y *= sc;
+    gs[threadIdx.x] = g;
+  }
   __syncthreads();
   Diag<R> dg;
   if (ep.flags & EPI_DIAG) dg.init(ep, L);
@@ -269,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_gate_small(
     const long long* __restrict__ counter, EpiParams ep, int store) {
   using C = typename CT<R>::C;
   const C* gp = gate_ptr(gate_base, stride, counter);
+  const R sc = (R)renorm_scale(ep.rn);
   Diag<R> dg;
   if (ep.flags & EPI_DIAG) dg.init(ep, L);
   const R cxh = (R)ep.cx_hi, cxl = (R)ep.cx_lo;
@@ -287,6 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_gate_small(
       C acc = czero<C>();
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc = cmac(acc, gp[4 * r + c], v[c]);
+      acc.x *= sc;
+      acc.y *= sc;
       w[r] = acc;
     }
     if (store) {

@@ -139,6 +139,17 @@ fsv::EpiParams epi_for(const sv_ctx* ctx, int flags, int bond, double* partial) 
   return ep;
 }
 
+fsv::Renorm renorm_of(const sv_ctx* ctx) {
+  fsv::Renorm rn;
+  if (ctx->params.renorm_every > 0) {
+    rn.ring = ctx->d_ring;
+    rn.ring_len = kRing;
+    rn.counter = ctx->d_counter;
+    rn.every = ctx->params.renorm_every;
+  }
+  return rn;
+}
+
 // Enqueue one plain-mode period on stream s.
 int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
   const int ng = (int)ctx->gates.size();
@@ -150,6 +161,7 @@ int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
     double* part = gt.epi ? ctx->d_part_evolve + (size_t)slot * ctx->maxb * 2 : nullptr;
     if (gt.epi) ++slot;
     fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
+    if (g == 0) ep.rn = renorm_of(ctx);
     const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
     SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
                                    ctx->d_counter, ep, 1, ctx->cfg, s),
@@ -252,6 +264,8 @@ int read_ring(sv_ctx* ctx, int64_t c0, int64_t count, double* e_out, double* n_o
     if (e_out) e_out[k] = buf[2 * k];
     if (n_out) n_out[k] = buf[2 * k + 1];
   }
+  if (ctx->block && fsv::block_status(ctx->block, ctx->stream) != 0)
+    return fail(ctx, SV_ETIMEOUT, "a tensor-core block pass gave up a bounded wait");
   return SV_OK;
 }
 
@@ -272,6 +286,7 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
     double* part = gt.epi ? ctx->d_part_evolve + (size_t)slot * ctx->maxb * 2 : nullptr;
     if (gt.epi) ++slot;
     fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
+    if (g == 0) ep.rn = renorm_of(ctx);
     const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
     SV_CUDA(cudaEventRecord(ev[g], s), "event record");
     SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
@@ -510,6 +525,7 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
     int rc = fsv::block_build(ctx->L, ctx->gates, ctx->obs, n, p->split, ctx->cfg,
                               &ctx->block, &msg);
     if (rc != SV_OK) return fail(ctx, rc, "block build: %s", msg.c_str());
+    fsv::block_set_renorm(ctx->block, renorm_of(ctx));
     fsv::block_info(ctx->block, &ctx->passes_per_period, &ctx->launches_per_period);
     ctx->build_bytes = fsv::block_upload_bytes(ctx->block);
   } else {
@@ -572,7 +588,6 @@ int sv_evolve(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out
   DeviceGuard dg(ctx->device);
   rc = ensure_graph(ctx);
   if (rc) return rc;
-  const int renorm = ctx->params.renorm_every;
   int64_t done = 0;
   while (done < periods) {
     const int64_t chunk = std::min<int64_t>(periods - done, kRing);
@@ -580,10 +595,6 @@ int sv_evolve(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out
     for (int64_t k = 0; k < chunk; ++k) {
       SV_CUDA(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
       ++ctx->counter;
-      if (renorm > 0 && ctx->counter % renorm == 0)
-        SV_CUDA(fsv::launch_renormalize(ctx->precision, ctx->state, ctx->L, ctx->d_ring, kRing,
-                                        ctx->d_counter, ctx->cfg, ctx->stream),
-                "renormalize launch");
     }
     if (energy_out || norm_out) {
       rc = read_ring(ctx, c0, chunk, energy_out ? energy_out + done : nullptr,
@@ -619,11 +630,6 @@ int sv_evolve_profiled(sv_ctx* ctx, int64_t periods, double* energy_out, double*
     rc = enqueue_period_profiled(ctx, ctx->stream, ev.data());
     if (rc) break;
     ++ctx->counter;
-    if (ctx->params.renorm_every > 0 && ctx->counter % ctx->params.renorm_every == 0) {
-      cudaError_t e = fsv::launch_renormalize(ctx->precision, ctx->state, ctx->L, ctx->d_ring,
-                                              kRing, ctx->d_counter, ctx->cfg, ctx->stream);
-      if (e != cudaSuccess) rc = cuda_fail(ctx, e, "renormalize launch");
-    }
     if (rc == SV_OK) {
       cudaError_t e = cudaEventSynchronize(ev[nl]);
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "event synchronize");
@@ -700,6 +706,18 @@ int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period
           "set counter");
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
   ctx->counter = period;
+  if (period > 0 && ctx->built) {
+    // the folded renormalisation of the next period reads the norm recorded
+    // for period - 1: record the norm of the state just set
+    double n2 = 1.0;
+    rc = measure(ctx, nullptr, &n2);
+    if (rc) return rc;
+    const int64_t slot = (period - 1) % kRing;
+    SV_CUDA(cudaMemcpyAsync(ctx->d_ring + 2 * slot + 1, &n2, sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->stream),
+            "record norm");
+    SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  }
   return SV_OK;
 }
 
@@ -712,6 +730,15 @@ int sv_pass_info(const sv_ctx* ctx, int* passes_per_period, int* gates_per_perio
   if (passes_per_period) *passes_per_period = ctx->passes_per_period;
   if (gates_per_period) *gates_per_period = (int)ctx->gates.size();
   if (launches_per_period) *launches_per_period = ctx->launches_per_period;
+  return SV_OK;
+}
+
+int sv_form_info(const sv_ctx* ctx, int* tensor_cores, int* block_n) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->built) return SV_ESTATE;
+  const bool blk = ctx->params.mode == SV_MODE_BLOCK && ctx->block;
+  if (tensor_cores) *tensor_cores = blk && ctx->block->tensor_cores ? 1 : 0;
+  if (block_n) *block_n = blk ? ctx->block->n : 0;
   return SV_OK;
 }
 

@@ -55,11 +55,17 @@ struct BlockPlan {
   int maxb = 0;
   int grid = 0;
   LaunchCfg cfg;
+  // tensor-core pass: one TMA descriptor per pass for the attached state
+  std::vector<uint8_t> maps;   // passes x block_tc_map_bytes()
+  void* maps_psi = nullptr;    // state pointer the descriptors were built for
+  int* d_status = nullptr;     // raised by a pass whose bounded wait gave up
 };
 
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
                 int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg);
 void block_info(const BlockPlan* bp, int* passes, int* launches);
+// Fold the periodic renormalisation into the period's first pass.
+void block_set_renorm(BlockPlan* bp, const Renorm& rn);
 size_t block_upload_bytes(const BlockPlan* bp);
 cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
                                  int ring_len, cudaStream_t s);
@@ -70,10 +76,17 @@ cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* cou
                                         cudaEvent_t* ev);
 void block_free(BlockPlan* bp);
 
+// Nonzero if a tensor-core pass reported a timed-out wait (synchronises s).
+int block_status(BlockPlan* bp, cudaStream_t s);
+
 // CUDA-core FP32 pass (any n, R); tensor-core pass (n = 6, R = 7).
 cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
-cudaError_t launch_block_tc(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
+cudaError_t launch_block_tc(const PassArgs& pa, const void* map, int* status, int grid,
+                            cudaStream_t s);
 bool block_tc_supported(int L, int n);
+cudaError_t block_tc_prepare();
+size_t block_tc_map_bytes();
+int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out);
 // Bytes of the tensor-core operand block of one pass, and its host layout.
 size_t block_tc_w_bytes(int n);
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);

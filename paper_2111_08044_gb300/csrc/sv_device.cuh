@@ -136,6 +136,15 @@ __device__ inline void block_store_pair(double e, double n, double* out) {
   }
 }
 
+// Scale factor of the folded renormalisation (1 when this pass does none).
+__device__ __forceinline__ double renorm_scale(const Renorm& rn) {
+  if (!rn.ring || rn.every <= 0) return 1.0;
+  const long long c = *rn.counter;
+  if (c <= 0 || c % rn.every != 0) return 1.0;
+  const double n2 = rn.ring[2 * ((c - 1) % rn.ring_len) + 1];
+  return n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+}
+
 template <typename C>
 __device__ __forceinline__ const C* gate_ptr(const C* base, long long stride,
                                              const long long* counter) {

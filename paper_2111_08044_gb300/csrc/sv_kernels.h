@@ -7,6 +7,16 @@
 
 namespace fsv {
 
+// Renormalisation folded into the first pass of a period: when the period
+// counter c > 0 is a multiple of `every`, the pass scales what it writes by
+// 1/sqrt(norm of period c-1), read from the energy ring.
+struct Renorm {
+  const double* ring = nullptr;
+  int ring_len = 0;
+  const long long* counter = nullptr;
+  int every = 0;
+};
+
 // Energy terms measured by a plain gate pass, in the layout of the state
 // pass that applies the gate (site i = bit i).
 struct EpiParams {
@@ -18,6 +28,7 @@ struct EpiParams {
   double cz_first = 0.0;   // Z coefficient of site 0
   double cz_last = 0.0;    // Z coefficient of site L-1
   double* partial = nullptr;  // [gridDim.x][2] (energy, norm) of this launch
+  Renorm rn;                  // set on the first pass of a period only
 };
 
 struct LaunchCfg {

@@ -142,6 +142,13 @@ class FloquetSimulator:
                    self._ctx, "sv_evolve_profiled")
         return e[:periods], n[:periods], ms
 
+    def form_info(self):
+        """(tensor_cores, block_n) of the built evolution."""
+        tc, n = ctypes.c_int(), ctypes.c_int()
+        capi.check(self._lib.sv_form_info(self._ctx, ctypes.byref(tc), ctypes.byref(n)),
+                   self._ctx, "sv_form_info")
+        return bool(tc.value), n.value
+
     def build_bytes(self) -> int:
         b = ctypes.c_size_t()
         capi.check(self._lib.sv_build_bytes(self._ctx, ctypes.byref(b)), self._ctx,

@@ -9,11 +9,13 @@ from paper_2111_08044_gb300 import capi, inputs
 pytestmark = pytest.mark.gpu
 
 
-def _run_block(cfg, n, split, periods):
+def _run_block(cfg, n, split, periods, expect_tc=None):
     from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
     with FloquetSimulator(cfg.L) as sim:
         sim.init_product_state(cfg.spinors())
         sim.build(**chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=n, split=split))
+        if expect_tc is not None:
+            assert sim.form_info() == (expect_tc, n)
         e, nn = sim.evolve(periods)
         return e, nn, sim.host_state(), sim.pass_info()
 
@@ -26,7 +28,7 @@ BLOCK_CASES = [(8, 3), (8, 4), (10, 5), (12, 6), (12, 7), (13, 6), (14, 5), (16,
 def test_simt_block_form_matches_oracle(svlib, L, n):
     cfg = inputs.ChainConfig(L=L, periods=4, seed=60 + L)
     psi_o, _, e_o, n_o = orc.run_chain(cfg)
-    e, nn, psi, info = _run_block(cfg, n, capi.SV_SPLIT_FP32, cfg.periods)
+    e, nn, psi, info = _run_block(cfg, n, capi.SV_SPLIT_FP32, cfg.periods, expect_tc=False)
     assert info[0] >= 1
     err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
     assert err < 1e-5, err
@@ -43,12 +45,38 @@ def test_block_small_preset_100_periods(svlib):
     assert 1 - abs(ov) ** 2 < 1e-5
 
 
-@pytest.mark.parametrize("L", [14, 16, 20])
+def _infidelity(a, b):
+    a = a.astype(np.complex128)
+    b = b.astype(np.complex128)
+    return 1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+@pytest.mark.parametrize("L", [13, 14, 16, 20])
 def test_tensor_core_block_form_matches_oracle(svlib, L):
+    """tcgen05 TF32x3 block passes against the oracle.  The tensor-core
+    accumulation shrinks the norm by a few 1e-7 per pass (no renormalisation
+    here), so states are compared after normalisation and the norm drift is
+    bounded separately; energy densities are of the normalised state."""
     cfg = inputs.ChainConfig(L=L, periods=3, seed=80 + L)
     psi_o, _, e_o, n_o = orc.run_chain(cfg)
-    e, nn, psi, _ = _run_block(cfg, 6, capi.SV_SPLIT_TF32X3, cfg.periods)
-    err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
-    assert err < 1e-5, err
+    e, nn, psi, _ = _run_block(cfg, 6, capi.SV_SPLIT_TF32X3, cfg.periods, expect_tc=True)
+    assert _infidelity(psi, psi_o) < 1e-10
     np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
-    np.testing.assert_allclose(nn, n_o, atol=2e-6, rtol=0)
+    assert np.all(np.abs(nn - 1.0) < 2e-5 * np.arange(1, cfg.periods + 1))
+
+
+@pytest.mark.parametrize("L", [14, 17])
+def test_tensor_core_100_periods_with_renormalisation(svlib, L):
+    from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
+    cfg = inputs.ChainConfig(L=L, periods=100, seed=90 + L)
+    psi_o, _, e_o, _ = orc.run_chain(cfg)
+    with FloquetSimulator(cfg.L) as sim:
+        sim.init_product_state(cfg.spinors())
+        sim.build(**chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=6,
+                                 split=capi.SV_SPLIT_TF32X3, renorm_every=1))
+        assert sim.form_info() == (True, 6)
+        e, nn = sim.evolve(cfg.periods)
+        psi = sim.host_state()
+    np.testing.assert_allclose(e, e_o, atol=1e-5, rtol=0)
+    assert np.all(np.abs(nn - 1.0) < 2e-5)  # one period of drift at most
+    assert _infidelity(psi, psi_o) < 1e-5

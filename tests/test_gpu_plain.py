@@ -123,6 +123,22 @@ def test_per_period_parameters(svlib):
     np.testing.assert_allclose(psi, psi_o, atol=1e-12, rtol=0)
 
 
+def test_folded_renormalisation_plain(svlib):
+    """renorm_every folds a rescale into the first gate pass of a period."""
+    from paper_2111_08044_gb300.sim import chain_params
+    cfg = inputs.ChainConfig(L=11, periods=20, seed=12)
+    _, _, e_o, _ = orc.run_chain(cfg)
+    with _sim(cfg.L) as sim:
+        sim.init_product_state(cfg.spinors())
+        psi0 = sim.host_state()
+        sim.set_host_state(psi0 * 1.1, period=0)
+        sim.build(**chain_params(cfg, renorm_every=2))
+        e, n = sim.evolve(cfg.periods)
+    np.testing.assert_allclose(e, e_o, atol=1e-5, rtol=0)
+    assert abs(n[0] - 1.21) < 1e-5 and abs(n[1] - 1.21) < 1e-5  # no rescale before period 2
+    assert np.all(np.abs(n[1::2][1:] - 1.0) < 1e-5)  # rescaled at periods 2, 4, ...
+
+
 def test_call_order_errors(svlib):
     from paper_2111_08044_gb300 import capi
     with _sim(8) as sim:

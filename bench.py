@@ -40,7 +40,7 @@ def _parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--L", type=int, default=L_BENCH)
     ap.add_argument("--n", type=int, default=6, help="block width of the fused form")
-    ap.add_argument("--split", choices=["tf32x3", "fp32"], default="tf32x3")
+    ap.add_argument("--split", choices=["bf16x3", "fp32"], default="bf16x3")
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -140,7 +140,7 @@ def _time_form(args, mode, steps, rank, world, local):
     from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
 
     cfg = inputs.ChainConfig(L=args.L, seed=4 + rank)
-    split = capi.SV_SPLIT_TF32X3 if args.split == "tf32x3" else capi.SV_SPLIT_FP32
+    split = capi.SV_SPLIT_BF16X3 if args.split == "bf16x3" else capi.SV_SPLIT_FP32
     kw = chain_params(cfg)
     if mode == "block":
         kw.update(mode=capi.SV_MODE_BLOCK, block_n=args.n, split=split)
@@ -191,7 +191,7 @@ def _e2e(args, steps, rank, local):
 
     cfg = inputs.ChainConfig(L=args.L, seed=4 + rank)
     kw = chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=args.n,
-                      split=capi.SV_SPLIT_TF32X3 if args.split == "tf32x3" else capi.SV_SPLIT_FP32)
+                      split=capi.SV_SPLIT_BF16X3 if args.split == "bf16x3" else capi.SV_SPLIT_FP32)
     sim = FloquetSimulator(cfg.L, device=local)
     spinors = cfg.spinors()
     torch.cuda.synchronize()
@@ -298,7 +298,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_block / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (complex64 state; block GEMMs "
-        + ("TF32x3 split" if args.split == "tf32x3" else "FP32") + ", FP64 reductions)",
+        + ("tensor cores on exact bf16 digits, FP32 accumulators" if args.split == "bf16x3" else "FP32") + ", FP64 reductions)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": f"block n={args.n} {args.split}",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

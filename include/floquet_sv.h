@@ -62,7 +62,7 @@ extern "C" {
 #define SV_MODE_BLOCK 1 /* fused n-qubit blocks on the tensor cores */
 
 /* arithmetic of the block form */
-#define SV_SPLIT_TF32X3 0 /* hi/lo TF32 operands, 3 products, FP32 accumulate */
+#define SV_SPLIT_BF16X3 0 /* tensor cores: 3 exact bf16 digits per operand, exact level-0 sum */
 #define SV_SPLIT_FP32 1   /* FP32 CUDA-core block apply (reference form) */
 
 typedef struct sv_ctx sv_ctx;

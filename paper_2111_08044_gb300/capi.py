@@ -25,7 +25,7 @@ SV_C64 = 0
 SV_C128 = 1
 SV_MODE_PLAIN = 0
 SV_MODE_BLOCK = 1
-SV_SPLIT_TF32X3 = 0
+SV_SPLIT_BF16X3 = 0
 SV_SPLIT_FP32 = 1
 
 _ERRNAMES = {SV_EINVAL: "SV_EINVAL", SV_ENOMEM: "SV_ENOMEM", SV_ECUDA: "SV_ECUDA",
@@ -132,7 +132,7 @@ def check(rc: int, ctx=None, what: str = ""):
 
 
 def make_params(J=1.0, hx=0.9, hz=0.4, T=0.5, theta=0.3, edge_field_weight=0.5, K=4,
-                first_layer=0, mode=SV_MODE_PLAIN, block_n=0, split=SV_SPLIT_TF32X3,
+                first_layer=0, mode=SV_MODE_PLAIN, block_n=0, split=SV_SPLIT_BF16X3,
                 renorm_every=0, theta_p=None, hx_p=None):
     """sv_floquet_params plus the arrays it points to (keep both alive)."""
     import numpy as np

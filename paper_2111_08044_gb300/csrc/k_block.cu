@@ -161,7 +161,7 @@ cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStrea
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
                 int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg) {
   *out = nullptr;
-  if (split != SV_SPLIT_TF32X3 && split != SV_SPLIT_FP32) {
+  if (split != SV_SPLIT_BF16X3 && split != SV_SPLIT_FP32) {
     *msg = "unknown split";
     return SV_EINVAL;
   }
@@ -174,7 +174,7 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   bp->passes = fusion_plan(L, gates, n);
   const int P = (int)bp->passes.size();
   const int R = bp->R;
-  bp->tensor_cores = split == SV_SPLIT_TF32X3 && block_tc_supported(L, n);
+  bp->tensor_cores = split == SV_SPLIT_BF16X3 && block_tc_supported(L, n);
   const long long ntiles = 1ll << (L - n - R);
   const int per_sm = bp->tensor_cores ? 1 : 2;
   bp->grid = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)cfg.num_sms * per_sm));
@@ -331,7 +331,7 @@ cudaError_t ensure_maps(BlockPlan* bp, void* psi) {
 
 cudaError_t launch_pass(BlockPlan* bp, size_t k, void* psi, cudaStream_t s) {
   if (bp->tensor_cores)
-    return launch_block_tc(bp->args[k], bp->maps.data() + k * block_tc_map_bytes(),
+    return launch_block_tc(bp->args[k], psi, bp->maps.data() + k * block_tc_map_bytes(),
                            bp->d_status, bp->grid, s);
   return launch_block_simt(bp->args[k], psi, bp->grid, s);
 }

@@ -2,25 +2,43 @@
 // complex amplitudes (a window of n = 6 sites), the matrix-unit form of the
 // paper's fused-gate contraction (Sec. II, Eq. 2 on fused operators).
 //
-// Per CTA (one per SM, persistent over tiles):
-//   warp 8      TMA producer: four 128-row x 128-byte boxes per tile
-//               (cp.async.bulk.tensor.5d, 128-byte swizzle) into a
-//               double-buffered stage, plus the pass's operand block W once.
-//   warps 0-3   converters: thread = row = TMEM lane; split every real and
-//               imaginary part x into TF32 hi = rna(x), lo = rna(x - hi) and
-//               store four de-interleaved planes Sr_hi, Si_hi, Sr_lo, Si_lo
-//               into TMEM (tcgen05.st), the A operand.
-//   warp 9      allocates TMEM (512 columns) and issues the MMAs:
-//               D_re = Sr Ur^T - Si Ui^T, D_im = Sr Ui^T + Si Ur^T, each
-//               product as hi*hi + hi*lo + lo*hi (TF32 x3 split, FP32
-//               accumulate), M=128 N=64 K=8 tcgen05.mma.kind::tf32 with A in
-//               TMEM and B = [Ur|Ui]_[hi|lo] resident in shared memory
-//               (K-major, no swizzle); D double-buffered in TMEM.
-//   warps 4-7   epilogue: tcgen05.ld of D, energy terms (<X> on window
-//               sites in-row, the diagonal part on the natural layout of the
-//               period's last pass), the fused relabel (write each amplitude
-//               at its place in the next window's layout) into the stage
-//               buffer, then a TMA store of the tile.
+// Arithmetic.  The FP32 accumulator of tcgen05.mma truncates toward zero
+// when it aligns products and when it adds to D, which biases a long
+// evolution (measured: a dissipative drift of the energy density).  The
+// full-magnitude part of the product is therefore accumulated exactly:
+//   - each state row (64 complex = 128 reals) is scaled by a power of two
+//     2^(7-e_r) with 2^e_r >= max |x| and cut into three balanced 8-bit
+//     digits, x = 2^(e_r-7) (s0 + s1/256 + s2/65536), |s| <= 128, each
+//     rounded to nearest (the residual is below 2^-24 of the row's largest
+//     entry, as for FP32 rounding);
+//   - each entry of the fused unitary likewise, u = 2^-7 (u0 + u1/256 +
+//     u2/65536);
+//   - digits are bf16 values d, d/256, d/65536 (exact), so s0 u0 products
+//     are integers below 2^14 and their sum over K = 64 (both complex parts)
+//     stays below 2^21: the level-0 accumulator is EXACT; all other products
+//     (s0u1, s1u0, s0u2, s1u1, s2u0) are at most 2^-8 of the total and go to
+//     a second accumulator, whose truncation is 2^-8 smaller relative to the
+//     result (kind::f16 with bf16 inputs, FP32 accumulators in TMEM);
+//   - the epilogue adds the two with round-to-nearest FP32 arithmetic,
+//     out = 2^(e_r - 14) (L0 + R).
+//
+// Per CTA (one per SM, persistent over tiles), 8 warps:
+//   warps 0-3   converters: thread = row = TMEM lane; digits of the row into
+//               TMEM (tcgen05.st) as the A operand, in two K-halves so that
+//               the next tile's conversion overlaps the current tile's MMAs.
+//               Lane 0 of warp 0 also allocates TMEM (512 columns), keeps the
+//               TMA producer going (four 128-row x 128-byte boxes per tile,
+//               cp.async.bulk.tensor.5d with 128-byte swizzle, into a
+//               double-buffered stage refilled as soon as its rows are in
+//               registers, so two tiles of loads stay in flight;
+//               the pass's six 64x64 bf16 digit matrices once) and issues the
+//               96 MMAs of each tile (M=128, N=64, K=16, A in TMEM, B in
+//               shared memory).
+//   warps 4-7   epilogue: tcgen05.ld of the two accumulators, energy terms
+//               (<X> of window sites in-row; the diagonal part on the natural
+//               layout of the period's last pass), the fused relabel into a
+//               32 KiB staging buffer of output rows, then coalesced 16-byte
+//               stores of whole output rows, in two 64-row rounds.
 // Every wait is an mbarrier try_wait loop bounded by a clock budget; on
 // timeout the CTA raises *status, drains its own copies and MMAs, frees
 // TMEM and exits.
@@ -44,21 +62,26 @@ using namespace dev;
 constexpr int kN = 6;                 // window width
 constexpr int kCols = 1 << kN;        // complex amplitudes per row
 constexpr int kRows = 128;            // tile rows = MMA M = TMEM lanes
-constexpr int kThreads = 320;         // 10 warps
+constexpr int kThreads = 256;         // 8 warps (more threads cap registers at 168)
 constexpr uint32_t kStageBytes = kRows * kCols * 8;  // 64 KiB
-constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KiB
-constexpr uint32_t kMatBytes = kCols * kCols * 4;     // one 64 x 64 TF32 matrix
-constexpr uint32_t kWBytes = 6 * kMatBytes;           // Ur, Ui in three parts: 96 KiB
+constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KiB (one 128-byte column box)
+constexpr uint32_t kOutRowStride = 520;               // staging row: 512 B + 8 B pad
+constexpr uint32_t kOutBytes = 64 * kOutRowStride;    // 64 output rows per round
+constexpr uint32_t kMatBytes = kCols * kCols * 2;     // one 64 x 64 bf16 matrix
+constexpr uint32_t kWBytes = 6 * kMatBytes;           // Ur, Ui in three digits: 48 KiB
 constexpr uint32_t kOffW = 0;
 constexpr uint32_t kOffStage = kWBytes;
-constexpr uint32_t kOffMisc = kOffStage + 2 * kStageBytes;
-constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;  // misc + alignment slack
-// TMEM columns.  The A operand is two K-halves (k < 32, k >= 32) of 128
-// columns each, so the next tile's conversion can fill one half while the
-// MMAs read the other: half h = [128 h, 128 h + 128) holds Sr_hi, Si_hi,
-// Sr_lo, Si_lo for its 32 k's at offsets 0, 32, 64, 96.
-constexpr uint32_t kColSrHi = 0, kColSiHi = 32, kColSrLo = 64, kColSiLo = 96;
-constexpr uint32_t kColD = 256;  // D buffer b at kColD + 128 b: re [0,64), im [64,128)
+constexpr uint32_t kOffOut = kOffStage + 2 * kStageBytes;
+constexpr uint32_t kOffMisc = (kOffOut + kOutBytes + 1023) & ~1023u;
+constexpr uint32_t kMiscBytes = 2048;
+constexpr uint32_t kSmemBytes = kOffMisc + kMiscBytes + 1024;  // + alignment slack
+// TMEM columns: A (bf16 pairs) in two K-halves of 96 columns: half h at
+// 96 h holds the s0 / s1 / s2 digit planes of the real and imaginary parts
+// for k in [32 h, 32 h + 32) at offsets 0, 16, 32 (real) and 48, 64, 80
+// (imaginary).  Accumulators after it.
+constexpr uint32_t kAHalf = 96;
+constexpr uint32_t kColR0 = 0, kColR1 = 16, kColR2 = 32, kColI0 = 48, kColI1 = 64, kColI2 = 80;
+constexpr uint32_t kColAcc = 192;  // L0re, L0im, Rre, Rim (64 each)
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 // misc block layout (offsets from kOffMisc)
@@ -67,14 +90,14 @@ enum : uint32_t {
   kBarW = 16,       // operand block loaded
   kBarAReady = 24,  // 2 x 8: A half h written
   kBarAFree = 40,   // 2 x 8: A half h consumed by the MMAs
-  kBarDFull = 56,   // 2 x 8: D buffer b complete
-  kBarDFree = 72,   // 2 x 8: D buffer b read out
-  kBarSFree = 88,   // 2 x 8: stage b stored out
-  kBarMmaDone = 104,
-  kTmemSlot = 112,
-  kAbort = 116,
-  kSigmaCol = 128,  // 64 x uint16
+  kBarDFull = 56,   // accumulators complete
+  kBarDFree = 64,   // accumulators read out
+  kBarSFree = 72,   // 2 x 8: stage b converted
+  kBarMmaDone = 88,
+  kTmemSlot = 96,
+  kAbort = 100,
   kRed = 256,       // 4 x 2 doubles
+  kExp = 512,       // 2 x 128 int: row exponents per tile parity
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -130,6 +153,7 @@ __device__ __forceinline__ bool epilogue_all_ok(bool ok) {
       : "memory");
   return any_bad == 0;
 }
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int c0, int c1, int c2, int c3, int c4) {
@@ -157,12 +181,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -170,13 +188,11 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
-      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-      "r"(v[15])
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
       : "memory");
 }
 
@@ -192,8 +208,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 // Shared-memory matrix descriptor: K-major, no swizzle, core matrices of
-// 8 rows x 16 bytes; LBO = 1024 B between core matrices along K, SBO = 128 B
-// between 8-row groups along N.
+// 8 rows x 16 bytes (8 bf16); LBO = 1024 B between core matrices along K,
+// SBO = 128 B between 8-row groups along N.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -203,18 +219,18 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
-// N = 64, M = 128, optional negation of B.
+// Instruction descriptor: kind::f16 with D = F32, A = B = BF16, both
+// K-major, N = 64, M = 128, optional negation of B.
 __host__ __device__ constexpr uint32_t make_idesc(int negate_b) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)negate_b << 14) |
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)negate_b << 14) |
          ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
       "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -225,8 +241,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
+// Two values with at most 8 significant bits each (exact in bf16), packed
+// as bf16x2 with `lo` in the low half.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
-    k_block_tc(const __grid_constant__ CUtensorMap tmap, PassArgs pa, int* status) {
+    k_block_tc(const __grid_constant__ CUtensorMap tmap_in, PassArgs pa, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -234,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* misc = smem + kOffMisc;
   const uint32_t mbase = sbase + kOffMisc;
   volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(misc + kAbort);
-  uint16_t* sigma_col = reinterpret_cast<uint16_t*>(misc + kSigmaCol);
+  int* row_exp = reinterpret_cast<int*>(misc + kExp);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = pa.a;
   const long long ntiles = pa.ntiles;
@@ -250,22 +274,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(mbase + kBarAFree, 1);
     mbar_init(mbase + kBarAFree + 8, 1);
     mbar_init(mbase + kBarDFull, 1);
-    mbar_init(mbase + kBarDFull + 8, 1);
     mbar_init(mbase + kBarDFree, 128);
-    mbar_init(mbase + kBarDFree + 8, 128);
-    mbar_init(mbase + kBarSFree, 1);
-    mbar_init(mbase + kBarSFree + 8, 1);
+    mbar_init(mbase + kBarSFree, 128);
+    mbar_init(mbase + kBarSFree + 8, 128);
     mbar_init(mbase + kBarMmaDone, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (threadIdx.x < kCols) {  // output-tile bits contributed by column bits
-    uint32_t y = 0;
-    for (int q = 0; q < kN; ++q) y |= ((threadIdx.x >> q) & 1u) << pa.sigma[q];
-    sigma_col[threadIdx.x] = (uint16_t)y;
-  }
-  if (warp == 9) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      mbase + kTmemSlot)
                  : "memory");
@@ -276,111 +293,67 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(misc + kTmemSlot);
 
-  if (warp == 8) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      mbar_expect_tx(mbase + kBarW, kWBytes);
-      const uint8_t* wsrc = static_cast<const uint8_t*>(pa.W);
-      for (int q = 0; q < 4; ++q)
-        bulk_load(sbase + kOffW + q * (kWBytes / 4), wsrc + q * (kWBytes / 4), kWBytes / 4,
-                  mbase + kBarW);
-      long long issued = 0;
-      for (long long i = 0; i < my_tiles; ++i) {
-        const int b = (int)(i & 1);
-        const uint32_t k = (uint32_t)(i >> 1);
-        if (i >= 2 && !wait_bar(mbase + kBarSFree + 8 * b, (k - 1) & 1, abort, status)) break;
-        const long long t = blockIdx.x + i * gridDim.x;
-        const int tlo = (int)(t & ((1ll << (a - kN)) - 1));
-        const int thi = (int)(t >> (a - kN));
-        const uint32_t bar = mbase + kBarFull + 8 * b;
-        mbar_expect_tx(bar, kStageBytes);
-        for (int c = 0; c < 4; ++c)
-          tma_load_5d(sbase + kOffStage + b * kStageBytes + c * kBoxBytes, &tmap, bar, 0, c, tlo,
-                      0, thi);
-        issued = i + 1;
-      }
-      // drain loads nobody will consume (abort path) before the CTA exits
-      for (long long i = issued - 2 < 0 ? 0 : issued - 2; i < issued && *abort; ++i) {
-        const int b = (int)(i & 1);
-        const long long t0 = clock64();
-        while (!mbar_try_wait(mbase + kBarFull + 8 * b, (uint32_t)((i >> 1) & 1)) &&
-               clock64() - t0 < kTimeoutCycles) {
-        }
-      }
-    }
-  } else if (warp == 9) {
-    // ---------------------------------------------------------------- MMA
-    if (lane == 0) {
-      bool ok = wait_bar(mbase + kBarW, 0, abort, status);
-      tc_fence_after();
-      const uint32_t w0 = sbase + kOffW;
-      // B operands: Ur and Ui in three TF32 parts each (hi, lo, lo2)
-      const uint64_t d_urh = make_desc(w0), d_url = make_desc(w0 + kMatBytes),
-                     d_url2 = make_desc(w0 + 2 * kMatBytes),
-                     d_uih = make_desc(w0 + 3 * kMatBytes),
-                     d_uil = make_desc(w0 + 4 * kMatBytes),
-                     d_uil2 = make_desc(w0 + 5 * kMatBytes);
-      constexpr uint32_t id_pos = make_idesc(0), id_neg = make_idesc(1);
-      for (long long i = 0; ok && i < my_tiles; ++i) {
-        const int b = (int)(i & 1);
-        const uint32_t k = (uint32_t)(i >> 1);
-        if (i >= 2 && !wait_bar(mbase + kBarDFree + 8 * b, (k - 1) & 1, abort, status)) break;
-        const uint32_t dre = tmem + kColD + 128 * b, dim = dre + 64;
-        bool half_ok = true;
-        for (int h = 0; h < 2 && half_ok; ++h) {
-          if (!wait_bar(mbase + kBarAReady + 8 * h, (uint32_t)(i & 1), abort, status)) {
-            half_ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t abase = tmem + 128 * h;
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            // global k-step 4h + ks: two core matrices (1024 B apart) along K
-            const uint64_t kofs = (uint64_t)((2 * (4 * h + ks) * 1024) >> 4);
-            const uint32_t acc = (h > 0 || ks > 0) ? 1u : 0u;
-            const uint32_t srh = abase + kColSrHi + 8 * ks, sih = abase + kColSiHi + 8 * ks;
-            const uint32_t srl = abase + kColSrLo + 8 * ks, sil = abase + kColSiLo + 8 * ks;
-            // D_re = Sr Ur^T - Si Ui^T with S = hi + lo, U = hi + lo + lo2
-            mma_tf32(dre, srh, d_urh + kofs, id_pos, acc);
-            mma_tf32(dre, srh, d_url + kofs, id_pos, 1);
-            mma_tf32(dre, srh, d_url2 + kofs, id_pos, 1);
-            mma_tf32(dre, srl, d_urh + kofs, id_pos, 1);
-            mma_tf32(dre, sih, d_uih + kofs, id_neg, 1);
-            mma_tf32(dre, sih, d_uil + kofs, id_neg, 1);
-            mma_tf32(dre, sih, d_uil2 + kofs, id_neg, 1);
-            mma_tf32(dre, sil, d_uih + kofs, id_neg, 1);
-            // D_im = Sr Ui^T + Si Ur^T
-            mma_tf32(dim, srh, d_uih + kofs, id_pos, acc);
-            mma_tf32(dim, srh, d_uil + kofs, id_pos, 1);
-            mma_tf32(dim, srh, d_uil2 + kofs, id_pos, 1);
-            mma_tf32(dim, srl, d_uih + kofs, id_pos, 1);
-            mma_tf32(dim, sih, d_urh + kofs, id_pos, 1);
-            mma_tf32(dim, sih, d_url + kofs, id_pos, 1);
-            mma_tf32(dim, sih, d_url2 + kofs, id_pos, 1);
-            mma_tf32(dim, sil, d_urh + kofs, id_pos, 1);
-          }
-          mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
-        }
-        if (!half_ok) break;
-        mma_commit(mbase + kBarDFull + 8 * b);
-      }
-      // all issued MMAs complete before TMEM is released
-      mma_commit(mbase + kBarMmaDone);
-      const long long t0 = clock64();
-      while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
-      }
-    }
-  } else if (warp < 4) {
-    // ---------------------------------------------------------- converters
+  if (warp < 4) {
+    // ---------------------------------------- converters (+ producer, MMA)
+    const bool leader = warp == 0 && lane == 0;
     const int r = warp * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (long long i = 0; i < my_tiles; ++i) {
+    const uint32_t w0 = sbase + kOffW;
+    auto load_tile = [&](long long i) {  // leader only
+      const int b = (int)(i & 1);
+      const long long t = blockIdx.x + i * gridDim.x;
+      const int tlo = (int)(t & ((1ll << (a - kN)) - 1));
+      const int thi = (int)(t >> (a - kN));
+      const uint32_t bar = mbase + kBarFull + 8 * b;
+      mbar_expect_tx(bar, kStageBytes);
+      for (int c = 0; c < 4; ++c)
+        tma_load_5d(sbase + kOffStage + b * kStageBytes + c * kBoxBytes, &tmap_in, bar, 0, c, tlo,
+                    0, thi);
+    };
+    long long issued = 0;
+    if (leader) {
+      mbar_expect_tx(mbase + kBarW, kWBytes);
+      const uint8_t* wsrc = static_cast<const uint8_t*>(pa.W);
+      for (int q = 0; q < 3; ++q)
+        bulk_load(w0 + q * (kWBytes / 3), wsrc + q * (kWBytes / 3), kWBytes / 3, mbase + kBarW);
+      for (; issued < 2 && issued < my_tiles; ++issued) load_tile(issued);
+    }
+    bool ok = true;
+    if (leader) {
+      ok = wait_bar(mbase + kBarW, 0, abort, status);
+      tc_fence_after();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    const uint64_t dr0 = make_desc(w0), dr1 = make_desc(w0 + kMatBytes),
+                   dr2 = make_desc(w0 + 2 * kMatBytes), di0 = make_desc(w0 + 3 * kMatBytes),
+                   di1 = make_desc(w0 + 4 * kMatBytes), di2 = make_desc(w0 + 5 * kMatBytes);
+    constexpr uint32_t ip = make_idesc(0), in = make_idesc(1);
+    const uint32_t l0r = tmem + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
+    for (long long i = 0; i < my_tiles && __all_sync(0xffffffffu, ok); ++i) {
       const int b = (int)(i & 1);
       const uint32_t k = (uint32_t)(i >> 1);
-      bool ok = wait_bar(mbase + kBarFull + 8 * b, k & 1, abort, status);
+      ok = wait_bar(mbase + kBarFull + 8 * b, k & 1, abort, status);
       if (__any_sync(0xffffffffu, !ok)) break;  // the warp leaves together
       const uint8_t* stage = smem + kOffStage + b * kStageBytes;
+      // the row (64 complex) into registers; exponent 2^e >= max |x|
+      float4 row[32];
+      float m = 0.f;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        row[q] = *reinterpret_cast<const float4*>(stage + (q >> 3) * kBoxBytes + r * 128 +
+                                                  (((q & 7) ^ (r & 7)) << 4));
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(row[q].x), fabsf(row[q].y)),
+                           fmaxf(fabsf(row[q].z), fabsf(row[q].w))));
+      }
+      // the stage is no longer needed: let the producer refill it now
+      mbar_arrive(mbase + kBarSFree + 8 * b);
+      if (leader && issued < my_tiles && issued == i + 2) {
+        ok = wait_bar(mbase + kBarSFree + 8 * b, k & 1, abort, status);
+        if (ok) load_tile(issued++);
+      }
+      int e = 0;
+      if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+      const float scale = ldexpf(1.f, 7 - e);
       for (int h = 0; h < 2 && ok; ++h) {
         if (i >= 1)
           ok = wait_bar(mbase + kBarAFree + 8 * h, (uint32_t)((i - 1) & 1), abort, status);
@@ -389,35 +362,114 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-#pragma unroll 1
+        // The exponent slot of this tile parity was last read by the epilogue
+        // of tile i - 2, before it released the accumulators for tile i - 1;
+        // A's first half being free for tile i means tile i - 1's MMAs ran.
+        if (h == 0) row_exp[(i & 1) * kRows + r] = e;
+#pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const int c = 2 * h + cc;  // 16-amplitude chunk, k in [16 c, 16 c + 16)
-          uint32_t rh[16], ih[16], rl[16], il[16];
-          const uint8_t* rowp = stage + c * kBoxBytes + r * 128;
+          uint32_t r0[8], r1[8], r2[8], i0[8], i1[8], i2[8];
 #pragma unroll
           for (int s = 0; s < 8; ++s) {
-            const float4 v = *reinterpret_cast<const float4*>(rowp + ((s ^ (r & 7)) << 4));
-            const float xs[4] = {v.x, v.y, v.z, v.w};
+            const float4 v = row[8 * c + s];
+            // amplitudes k = 16c + 2s and 16c + 2s + 1: (v.x, v.y), (v.z, v.w)
+            const float y[4] = {v.x * scale, v.y * scale, v.z * scale, v.w * scale};
+            float d0[4], d1[4], d2[4];
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const uint32_t hr = tf32_rna(xs[2 * e]), hi_ = tf32_rna(xs[2 * e + 1]);
-              rh[2 * s + e] = hr;
-              ih[2 * s + e] = hi_;
-              rl[2 * s + e] = tf32_rna(xs[2 * e] - __uint_as_float(hr));
-              il[2 * s + e] = tf32_rna(xs[2 * e + 1] - __uint_as_float(hi_));
+            for (int e2 = 0; e2 < 4; ++e2) {
+              d0[e2] = rintf(y[e2]);
+              const float t1 = (y[e2] - d0[e2]) * 256.f;  // exact
+              d1[e2] = rintf(t1);
+              d2[e2] = rintf((t1 - d1[e2]) * 256.f) * (1.f / 65536.f);
+              d1[e2] *= (1.f / 256.f);  // digits as d, d/256, d/65536: exact bf16
             }
+            r0[s] = pack_bf16x2(d0[0], d0[2]);
+            i0[s] = pack_bf16x2(d0[1], d0[3]);
+            r1[s] = pack_bf16x2(d1[0], d1[2]);
+            i1[s] = pack_bf16x2(d1[1], d1[3]);
+            r2[s] = pack_bf16x2(d2[0], d2[2]);
+            i2[s] = pack_bf16x2(d2[1], d2[3]);
           }
-          const uint32_t hb = lane_base + 128 * h + 16 * cc;
-          tmem_st16(hb + kColSrHi, rh);
-          tmem_st16(hb + kColSiHi, ih);
-          tmem_st16(hb + kColSrLo, rl);
-          tmem_st16(hb + kColSiLo, il);
+          const uint32_t hb = lane_base + kAHalf * h + 8 * cc;
+          tmem_st8(hb + kColR0, r0);
+          tmem_st8(hb + kColR1, r1);
+          tmem_st8(hb + kColR2, r2);
+          tmem_st8(hb + kColI0, i0);
+          tmem_st8(hb + kColI1, i1);
+          tmem_st8(hb + kColI2, i2);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         mbar_arrive(mbase + kBarAReady + 8 * h);
       }
-      if (!ok) break;
+      if (__any_sync(0xffffffffu, !ok)) break;
+      if (leader) {
+        // the MMAs of tile i once both halves of A are written and the
+        // epilogue has read out tile i - 1
+        for (int h = 0; h < 2 && ok; ++h)
+          ok = wait_bar(mbase + kBarAReady + 8 * h, (uint32_t)(i & 1), abort, status);
+        if (ok && i >= 1) ok = wait_bar(mbase + kBarDFree, (uint32_t)((i - 1) & 1), abort, status);
+        if (ok) {
+          tc_fence_after();
+          for (int h = 0; h < 2; ++h) {
+            const uint32_t ab = tmem + kAHalf * h;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              // global k-step 2h + ks (K = 16): two core matrices along K
+              const uint64_t ko = (uint64_t)((2 * (2 * h + ks) * 1024) >> 4);
+              const uint32_t acc = (h > 0 || ks > 0) ? 1u : 0u;
+              const uint32_t r0 = ab + kColR0 + 8 * ks, r1 = ab + kColR1 + 8 * ks,
+                             r2 = ab + kColR2 + 8 * ks;
+              const uint32_t i0 = ab + kColI0 + 8 * ks, i1 = ab + kColI1 + 8 * ks,
+                             i2 = ab + kColI2 + 8 * ks;
+              // level 0 (exact): s0 u0
+              mma_bf16(l0r, r0, dr0 + ko, ip, acc);
+              mma_bf16(l0r, i0, di0 + ko, in, 1);
+              mma_bf16(l0i, r0, di0 + ko, ip, acc);
+              mma_bf16(l0i, i0, dr0 + ko, ip, 1);
+              // rest: s0 u1 + s1 u0 + s0 u2 + s1 u1 + s2 u0
+              mma_bf16(rr_, r0, dr1 + ko, ip, acc);
+              mma_bf16(rr_, r1, dr0 + ko, ip, 1);
+              mma_bf16(rr_, r0, dr2 + ko, ip, 1);
+              mma_bf16(rr_, r1, dr1 + ko, ip, 1);
+              mma_bf16(rr_, r2, dr0 + ko, ip, 1);
+              mma_bf16(rr_, i0, di1 + ko, in, 1);
+              mma_bf16(rr_, i1, di0 + ko, in, 1);
+              mma_bf16(rr_, i0, di2 + ko, in, 1);
+              mma_bf16(rr_, i1, di1 + ko, in, 1);
+              mma_bf16(rr_, i2, di0 + ko, in, 1);
+              mma_bf16(ri_, r0, di1 + ko, ip, acc);
+              mma_bf16(ri_, r1, di0 + ko, ip, 1);
+              mma_bf16(ri_, r0, di2 + ko, ip, 1);
+              mma_bf16(ri_, r1, di1 + ko, ip, 1);
+              mma_bf16(ri_, r2, di0 + ko, ip, 1);
+              mma_bf16(ri_, i0, dr1 + ko, ip, 1);
+              mma_bf16(ri_, i1, dr0 + ko, ip, 1);
+              mma_bf16(ri_, i0, dr2 + ko, ip, 1);
+              mma_bf16(ri_, i1, dr1 + ko, ip, 1);
+              mma_bf16(ri_, i2, dr0 + ko, ip, 1);
+            }
+            mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
+          }
+          mma_commit(mbase + kBarDFull);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0) && ok;
+    }
+    if (leader) {
+      // drain loads nobody will consume (abort path) before the CTA exits
+      for (long long i = issued - 2 < 0 ? 0 : issued - 2; i < issued && *abort; ++i) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(mbase + kBarFull + 8 * (int)(i & 1), (uint32_t)((i >> 1) & 1)) &&
+               clock64() - t0 < kTimeoutCycles) {
+        }
+      }
+      // all issued MMAs complete before TMEM is released
+      mma_commit(mbase + kBarMmaDone);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
+      }
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -426,32 +478,53 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     uint32_t yrow = 0;  // output-tile bits contributed by this row's bits
     for (int bq = 0; bq < 7; ++bq) yrow |= ((uint32_t)(r >> bq) & 1u) << pa.sigma[kN + bq];
+    // Staging place of output element (ro, co) within its round:
+    // (ro & 63) * kOutRowStride + 8 co.  The relabel is a bit permutation, so
+    // the place of this row's element c is base + sum over set bits j of c of
+    // off[j], and its round (output bit 12) is bit c of a 64-bit mask.
+    const uint32_t base = ((yrow >> kN) & 63) * kOutRowStride + (yrow & (kCols - 1)) * 8;
+    uint32_t off[kN];
+    uint64_t round1 = 0;  // bit c: element c belongs to round 1
+#pragma unroll
+    for (int j = 0; j < kN; ++j) {
+      const int sj = pa.sigma[j];
+      off[j] = sj < kN ? (8u << sj) : (sj < kN + 6 ? (kOutRowStride << (sj - kN)) : 0u);
+    }
+    for (int c = 0; c < kCols; ++c) {
+      uint32_t yo = yrow;
+      for (int j = 0; j < kN; ++j)
+        if ((c >> j) & 1) yo |= 1u << pa.sigma[j];
+      round1 |= (uint64_t)((yo >> 12) & 1u) << c;
+    }
+    float2* const psi_g = static_cast<float2*>(pa.psi);
     Diag<float> dg;
     if (pa.diag) dg.init(pa.ep, pa.L);
     const float sc = (float)renorm_scale(pa.ep.rn);
     double eacc = 0.0, nacc = 0.0;
+    uint8_t* out = smem + kOffOut;
     for (long long i = 0; i < my_tiles; ++i) {
-      const int b = (int)(i & 1);
-      const uint32_t k = (uint32_t)(i >> 1);
-      const bool ok = wait_bar(mbase + kBarDFull + 8 * b, k & 1, abort, status);
+      const bool ok = wait_bar(mbase + kBarDFull, (uint32_t)(i & 1), abort, status);
       if (!epilogue_all_ok(ok)) break;  // the four epilogue warps leave together
       tc_fence_after();
+      const float rs = ldexpf(sc, row_exp[(i & 1) * kRows + r] - 14);
       float re[kCols], im[kCols];
-      const uint32_t dcol = lane_base + kColD + 128 * b;
+      const uint32_t acc = lane_base + kColAcc;
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
-        uint32_t vr[16], vi[16];
-        tmem_ld16(dcol + 16 * c4, vr);
-        tmem_ld16(dcol + 64 + 16 * c4, vi);
+        uint32_t v0[16], v1[16], w0[16], w1[16];
+        tmem_ld16(acc + 16 * c4, v0);        // L0 re
+        tmem_ld16(acc + 128 + 16 * c4, v1);  // R re
+        tmem_ld16(acc + 64 + 16 * c4, w0);   // L0 im
+        tmem_ld16(acc + 192 + 16 * c4, w1);  // R im
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          re[16 * c4 + e] = __uint_as_float(vr[e]) * sc;
-          im[16 * c4 + e] = __uint_as_float(vi[e]) * sc;
+          re[16 * c4 + e] = (__uint_as_float(v0[e]) + __uint_as_float(v1[e])) * rs;
+          im[16 * c4 + e] = (__uint_as_float(w0[e]) + __uint_as_float(w1[e])) * rs;
         }
       }
       tc_fence_before();
-      mbar_arrive(mbase + kBarDFree + 8 * b);  // D[b] may be overwritten
+      mbar_arrive(mbase + kBarDFree);  // the accumulators may be overwritten
       float es = 0.f, ns = 0.f;
       if (pa.x_mask) {
 #pragma unroll
@@ -467,34 +540,47 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t tlo = (uint64_t)t & ((1ull << (a - kN)) - 1);
       const uint64_t thi = (uint64_t)t >> (a - kN);
       const uint64_t tbase = (tlo << kN) | (thi << (a + 7));
-      uint8_t* stage = smem + kOffStage + b * kStageBytes;
+      // The relabelled tile leaves in two rounds of 64 output rows: scatter
+      // this row's amplitudes to their output places in the staging buffer,
+      // then copy whole output rows to global memory with coalesced 16-byte
+      // stores.
+#pragma unroll 1
+      for (int round = 0; round < 2; ++round) {
+        // offsets are recomputed per round rather than kept live (registers)
 #pragma unroll
-      for (int c = 0; c < kCols; ++c) {
-        const uint32_t yo = yrow | sigma_col[c];
-        const uint32_t ro = yo >> kN, co = yo & (kCols - 1);
-        uint8_t* dst = stage + (co >> 4) * kBoxBytes + ro * 128 +
-                       ((((co & 15) >> 1) ^ (ro & 7)) << 4) + ((co & 1) << 3);
-        *reinterpret_cast<float2*>(dst) = make_float2(re[c], im[c]);
-        if (pa.diag) {
-          const float p2 = re[c] * re[c] + im[c] * im[c];
-          ns += p2;
-          es += p2 * dg(tbase + ((uint64_t)ro << a) + co);
+        for (int j = 0; j < kN; ++j) asm volatile("" : "+r"(off[j]));
+        const uint64_t want = round ? round1 : ~round1;
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+          uint32_t o = base;
+#pragma unroll
+          for (int j = 0; j < kN; ++j)
+            if ((c >> j) & 1) o += off[j];
+          if ((want >> c) & 1) *reinterpret_cast<float2*>(out + o) = make_float2(re[c], im[c]);
         }
+        epilogue_sync();
+        // warp q copies output rows [16 q, 16 q + 16) of this round
+#pragma unroll 4
+        for (int k2 = 0; k2 < 16; ++k2) {
+          const uint32_t rr = 16 * q + k2;
+          const uint8_t* src = out + rr * kOutRowStride + 16 * lane;
+          const float2 lo = *reinterpret_cast<const float2*>(src);
+          const float2 hi = *reinterpret_cast<const float2*>(src + 8);
+          const float4 v = make_float4(lo.x, lo.y, hi.x, hi.y);
+          const uint64_t ro = 64 * round + rr;
+          const uint64_t x = tbase + (ro << a) + 2 * lane;  // natural index of (ro, 2 lane)
+          *reinterpret_cast<float4*>(psi_g + x) = v;
+          if (pa.diag) {
+            const float p0 = v.x * v.x + v.y * v.y, p1 = v.z * v.z + v.w * v.w;
+            ns += p0 + p1;
+            es += p0 * dg(x) + p1 * dg(x + 1);
+          }
+        }
+        epilogue_sync();  // the staging buffer may be refilled
       }
       eacc += (double)es;
       nacc += (double)ns;
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (q == 0 && lane == 0) {
-        for (int cc = 0; cc < 4; ++cc)
-          tma_store_5d(&tmap, sbase + kOffStage + b * kStageBytes + cc * kBoxBytes, 0, cc,
-                       (int)tlo, 0, (int)thi);
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        mbar_arrive(mbase + kBarSFree + 8 * b);
-      }
     }
-    if (q == 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     // energy partials of this CTA (fixed order)
     if (pa.partial) {
 #pragma unroll
@@ -507,7 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         red[2 * q] = eacc;
         red[2 * q + 1] = nacc;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      epilogue_sync();
       if (q == 0 && lane == 0) {
         pa.partial[2 * blockIdx.x] = (red[0] + red[2]) + (red[4] + red[6]);
         pa.partial[2 * blockIdx.x + 1] = (red[1] + red[3]) + (red[5] + red[7]);
@@ -516,7 +602,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
@@ -540,13 +626,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-uint32_t tf32_round_host(double x) {
-  float f = (float)x;
+uint16_t bf16_of_int(double v, double scale) {
+  // v is an integer with |v| <= 256 and scale a power of two: v * scale is
+  // exact in bf16 and in float
+  float f = (float)(v * scale);
   uint32_t u;
   std::memcpy(&u, &f, 4);
-  if ((u & 0x7F800000u) == 0x7F800000u) return u;  // inf / nan unchanged
-  u += 0xFFFu + ((u >> 13) & 1u);                   // round to nearest even at bit 13
-  return u & 0xFFFFE000u;
+  return (uint16_t)(u >> 16);
 }
 
 }  // namespace
@@ -556,28 +642,32 @@ bool block_tc_supported(int L, int n) { return n == kN && L >= kN + 7; }
 size_t block_tc_w_bytes(int n) { return n == kN ? kWBytes : 0; }
 
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
-  // six K-major 64 x 64 TF32 matrices Ur_hi, Ur_lo, Ur_lo2, Ui_hi, Ui_lo,
-  // Ui_lo2 (x = hi + lo + lo2 to about 33 bits) in the core-matrix order of
-  // make_desc: element (row j, col k) at word ((k/4)*8 + j/8)*32 + (j%8)*4 + k%4
+  // six K-major 64 x 64 bf16 digit matrices Ur0, Ur1, Ur2, Ui0, Ui1, Ui2
+  // holding u0, u1/256, u2/65536 with u = 2^-7 (u0 + u1/256 + u2/65536),
+  // |u_t| <= 128, in the core-matrix order
+  // of make_desc: element (row j, col k) at halfword
+  // ((k/8)*8 + j/8)*64 + (j%8)*8 + k%8
   out.assign(kWBytes / 4, 0u);
   if (n != kN) return;
+  std::vector<uint16_t> h(kWBytes / 2, 0);
   const size_t m = (size_t)kCols * kCols;
   for (int j = 0; j < kCols; ++j)
     for (int k = 0; k < kCols; ++k) {
       const cd u = U[(size_t)j * kCols + k];
-      const size_t w = (size_t)(((k >> 2) * 8 + (j >> 3)) * 32 + (j & 7) * 4 + (k & 3));
+      const size_t w = (size_t)(((k >> 3) * 8 + (j >> 3)) * 64 + (j & 7) * 8 + (k & 7));
       const double parts[2] = {u.real(), u.imag()};
       for (int ri = 0; ri < 2; ++ri) {
-        double rest = parts[ri];
+        double y = parts[ri] * 128.0;
+        double scale = 1.0;
         for (int q = 0; q < 3; ++q) {
-          const uint32_t t = tf32_round_host(rest);
-          float tf;
-          std::memcpy(&tf, &t, 4);
-          out[(size_t)(3 * ri + q) * m + w] = t;
-          rest -= (double)tf;
+          const double d = std::nearbyint(y);
+          h[(size_t)(3 * ri + q) * m + w] = bf16_of_int(d, scale);
+          y = (y - d) * 256.0;
+          scale /= 256.0;
         }
       }
     }
+  std::memcpy(out.data(), h.data(), kWBytes);
 }
 
 int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
@@ -586,10 +676,10 @@ int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
   const int a = pa.a, L = pa.L;
   cuuint64_t dims[5] = {32, 4, (cuuint64_t)1 << (a - kN), 128, (cuuint64_t)1 << (L - a - 7)};
   cuuint64_t strides[4] = {128, 512, (cuuint64_t)8 << a, (cuuint64_t)8 << (a + 7)};
-  cuuint32_t box[5] = {32, 1, 1, 128, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  cuuint32_t box_in[5] = {32, 1, 1, 128, 1};
   CUresult rc = fn(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, psi,
-                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   dims, strides, box_in, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return rc == CUDA_SUCCESS ? SV_OK : SV_ECUDA;
@@ -602,10 +692,12 @@ cudaError_t block_tc_prepare() {
                               (int)kSmemBytes);
 }
 
-cudaError_t launch_block_tc(const PassArgs& pa, const void* map, int* status, int grid,
-                            cudaStream_t s) {
-  const CUtensorMap& m = *static_cast<const CUtensorMap*>(map);
-  k_block_tc<<<grid, kThreads, kSmemBytes, s>>>(m, pa, status);
+cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int* status,
+                            int grid, cudaStream_t s) {
+  PassArgs p = pa;
+  p.psi = psi;
+  k_block_tc<<<grid, kThreads, kSmemBytes, s>>>(*static_cast<const CUtensorMap*>(map), p,
+                                                status);
   return cudaGetLastError();
 }
 

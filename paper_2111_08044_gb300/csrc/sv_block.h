@@ -37,6 +37,7 @@ struct PassArgs {
   int8_t sigma[16] = {};     // output tile bit of input tile bit q
   const float2* U = nullptr; // fused unitary, FP32, row-major 2^n x 2^n
   const void* W = nullptr;   // tensor-core operand block of this pass
+  void* psi = nullptr;       // state (set at launch)
   double* partial = nullptr; // per-CTA (energy, norm) pairs or nullptr
   int slot = -1;             // partials slot (host bookkeeping)
   EpiParams ep;              // diagonal coefficients
@@ -81,8 +82,8 @@ int block_status(BlockPlan* bp, cudaStream_t s);
 
 // CUDA-core FP32 pass (any n, R); tensor-core pass (n = 6, R = 7).
 cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
-cudaError_t launch_block_tc(const PassArgs& pa, const void* map, int* status, int grid,
-                            cudaStream_t s);
+cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int* status,
+                            int grid, cudaStream_t s);
 bool block_tc_supported(int L, int n);
 cudaError_t block_tc_prepare();
 size_t block_tc_map_bytes();

@@ -22,23 +22,28 @@
 //   - the epilogue adds the two with round-to-nearest FP32 arithmetic,
 //     out = 2^(e_r - 14) (L0 + R).
 //
-// Per CTA (one per SM, persistent over tiles), 8 warps:
+// Per CTA (one per SM, persistent over tiles), three warpgroups whose
+// register shares are rebalanced with setmaxnreg (168 a thread at launch,
+// 128 x (224 + 224 + 56) in total):
 //   warps 0-3   converters: thread = row = TMEM lane; digits of the row into
 //               TMEM (tcgen05.st) as the A operand, in two K-halves so that
 //               the next tile's conversion overlaps the current tile's MMAs.
-//               Lane 0 of warp 0 also allocates TMEM (512 columns), keeps the
-//               TMA producer going (four 128-row x 128-byte boxes per tile,
-//               cp.async.bulk.tensor.5d with 128-byte swizzle, into a
-//               double-buffered stage refilled as soon as its rows are in
-//               registers, so two tiles of loads stay in flight;
-//               the pass's six 64x64 bf16 digit matrices once) and issues the
-//               96 MMAs of each tile (M=128, N=64, K=16, A in TMEM, B in
-//               shared memory).
+//               Warp 0 also allocates TMEM (512 columns).
 //   warps 4-7   epilogue: tcgen05.ld of the two accumulators, energy terms
 //               (<X> of window sites in-row; the diagonal part on the natural
-//               layout of the period's last pass), the fused relabel into a
-//               32 KiB staging buffer of output rows, then coalesced 16-byte
-//               stores of whole output rows, in two 64-row rounds.
+//               layout of the period's last pass), then the fused relabel:
+//               each amplitude goes to its output place in a 64 KiB staging
+//               tile kept in the output's own order under the 128-byte
+//               swizzle (one XOR per amplitude, visiting the row in Gray-code
+//               order), and one TMA tensor store writes the tile back.
+//   warp 8      one thread issues the 96 MMAs of each tile (M=128, N=64,
+//               K=16, A in TMEM, B in shared memory), half by half.
+//   warp 9      one thread keeps the TMA producer going: the pass's six
+//               64x64 bf16 digit matrices once, then four 128-row x 128-byte
+//               boxes per tile (cp.async.bulk.tensor.5d, 128-byte swizzle)
+//               into a ring of six box slots; a slot is refilled as soon as
+//               the converters hold its rows in registers.
+//   warps 10-11 idle (they complete the third warpgroup for setmaxnreg).
 // Every wait is an mbarrier try_wait loop bounded by a clock budget; on
 // timeout the CTA raises *status, drains its own copies and MMAs, frees
 // TMEM and exits.
@@ -62,17 +67,16 @@ using namespace dev;
 constexpr int kN = 6;                 // window width
 constexpr int kCols = 1 << kN;        // complex amplitudes per row
 constexpr int kRows = 128;            // tile rows = MMA M = TMEM lanes
-constexpr int kThreads = 256;         // 8 warps (more threads cap registers at 168)
-constexpr uint32_t kStageBytes = kRows * kCols * 8;  // 64 KiB
+constexpr int kThreads = 384;         // three warpgroups; registers 224 / 224 / 56 a thread
+constexpr uint32_t kTileBytes = kRows * kCols * 8;   // 64 KiB
 constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KiB (one 128-byte column box)
-constexpr uint32_t kOutRowStride = 520;               // staging row: 512 B + 8 B pad
-constexpr uint32_t kOutBytes = 64 * kOutRowStride;    // 64 output rows per round
+constexpr int kSlots = 6;                             // input ring: 1.5 tiles of boxes
 constexpr uint32_t kMatBytes = kCols * kCols * 2;     // one 64 x 64 bf16 matrix
 constexpr uint32_t kWBytes = 6 * kMatBytes;           // Ur, Ui in three digits: 48 KiB
-constexpr uint32_t kOffW = 0;
-constexpr uint32_t kOffStage = kWBytes;
-constexpr uint32_t kOffOut = kOffStage + 2 * kStageBytes;
-constexpr uint32_t kOffMisc = (kOffOut + kOutBytes + 1023) & ~1023u;
+constexpr uint32_t kOffOut = 0;                       // output staging tile
+constexpr uint32_t kOffW = kOffOut + kTileBytes;
+constexpr uint32_t kOffRing = kOffW + kWBytes;
+constexpr uint32_t kOffMisc = kOffRing + kSlots * kBoxBytes;
 constexpr uint32_t kMiscBytes = 2048;
 constexpr uint32_t kSmemBytes = kOffMisc + kMiscBytes + 1024;  // + alignment slack
 // TMEM columns: A (bf16 pairs) in two K-halves of 96 columns: half h at
@@ -86,18 +90,18 @@ constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 // misc block layout (offsets from kOffMisc)
 enum : uint32_t {
-  kBarFull = 0,     // 2 x 8: stage b loaded
-  kBarW = 16,       // operand block loaded
-  kBarAReady = 24,  // 2 x 8: A half h written
-  kBarAFree = 40,   // 2 x 8: A half h consumed by the MMAs
-  kBarDFull = 56,   // accumulators complete
-  kBarDFree = 64,   // accumulators read out
-  kBarSFree = 72,   // 2 x 8: stage b converted
-  kBarMmaDone = 88,
-  kTmemSlot = 96,
-  kAbort = 100,
-  kRed = 256,       // 4 x 2 doubles
-  kExp = 512,       // 2 x 128 int: row exponents per tile parity
+  kBarFull = 0,      // kSlots x 8: box slot loaded
+  kBarEmpty = 48,    // kSlots x 8: box slot read by the converters
+  kBarW = 96,        // operand block loaded
+  kBarAReady = 104,  // 2 x 8: A half h written
+  kBarAFree = 120,   // 2 x 8: A half h consumed by the MMAs
+  kBarDFull = 136,   // accumulators complete
+  kBarDFree = 144,   // accumulators read out
+  kBarMmaDone = 152,
+  kTmemSlot = 160,
+  kAbort = 164,
+  kRed = 256,        // 4 x 2 doubles
+  kExp = 512,        // 2 x 128 int: row exponents per tile parity
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -164,13 +168,23 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       "r"(bar)
       : "memory");
 }
-__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
-                                             int c2, int c3, int c4) {
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
-      " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
-      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group"
+      " [%0, {%2, %3, %4}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
+}
+// Byte offset of a staging-tile byte under the 128-byte swizzle: the
+// 16-byte chunk index (bits 4-6) is XORed with the 128-byte line index
+// modulo 8 (bits 7-9).  Linear over XOR.
+__host__ __device__ constexpr uint32_t swz128(uint32_t b) { return b ^ (((b >> 7) & 7u) << 4); }
+// index of the lowest set bit of g > 0 (the bit a Gray code flips at step g)
+__host__ __device__ constexpr int low_bit(int g) {
+  int k = 0;
+  while (!((g >> k) & 1)) ++k;
+  return k;
 }
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
                                           uint32_t bar) {
@@ -250,7 +264,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-    k_block_tc(const __grid_constant__ CUtensorMap tmap_in, PassArgs pa, int* status) {
+    k_block_tc(const __grid_constant__ CUtensorMap tmap_in,
+               const __grid_constant__ CUtensorMap tmap_out, PassArgs pa, int* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -266,8 +281,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (threadIdx.x == 0) {
-    mbar_init(mbase + kBarFull, 1);
-    mbar_init(mbase + kBarFull + 8, 1);
+    for (int b = 0; b < kSlots; ++b) {
+      mbar_init(mbase + kBarFull + 8 * b, 1);
+      mbar_init(mbase + kBarEmpty + 8 * b, 128);
+    }
     mbar_init(mbase + kBarW, 1);
     mbar_init(mbase + kBarAReady, 128);
     mbar_init(mbase + kBarAReady + 8, 128);
@@ -275,8 +292,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(mbase + kBarAFree + 8, 1);
     mbar_init(mbase + kBarDFull, 1);
     mbar_init(mbase + kBarDFree, 128);
-    mbar_init(mbase + kBarSFree, 128);
-    mbar_init(mbase + kBarSFree + 8, 128);
     mbar_init(mbase + kBarMmaDone, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,64 +308,38 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(misc + kTmemSlot);
 
-  if (warp < 4) {
-    // ---------------------------------------- converters (+ producer, MMA)
-    const bool leader = warp == 0 && lane == 0;
+  const int wg = warp >> 2;
+  if (wg == 0) {
+    // ------------------------------------------------------------ converters
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
     const int r = warp * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    const uint32_t w0 = sbase + kOffW;
-    auto load_tile = [&](long long i) {  // leader only
-      const int b = (int)(i & 1);
-      const long long t = blockIdx.x + i * gridDim.x;
-      const int tlo = (int)(t & ((1ll << (a - kN)) - 1));
-      const int thi = (int)(t >> (a - kN));
-      const uint32_t bar = mbase + kBarFull + 8 * b;
-      mbar_expect_tx(bar, kStageBytes);
-      for (int c = 0; c < 4; ++c)
-        tma_load_5d(sbase + kOffStage + b * kStageBytes + c * kBoxBytes, &tmap_in, bar, 0, c, tlo,
-                    0, thi);
-    };
-    long long issued = 0;
-    if (leader) {
-      mbar_expect_tx(mbase + kBarW, kWBytes);
-      const uint8_t* wsrc = static_cast<const uint8_t*>(pa.W);
-      for (int q = 0; q < 3; ++q)
-        bulk_load(w0 + q * (kWBytes / 3), wsrc + q * (kWBytes / 3), kWBytes / 3, mbase + kBarW);
-      for (; issued < 2 && issued < my_tiles; ++issued) load_tile(issued);
-    }
     bool ok = true;
-    if (leader) {
-      ok = wait_bar(mbase + kBarW, 0, abort, status);
-      tc_fence_after();
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    const uint64_t dr0 = make_desc(w0), dr1 = make_desc(w0 + kMatBytes),
-                   dr2 = make_desc(w0 + 2 * kMatBytes), di0 = make_desc(w0 + 3 * kMatBytes),
-                   di1 = make_desc(w0 + 4 * kMatBytes), di2 = make_desc(w0 + 5 * kMatBytes);
-    constexpr uint32_t ip = make_idesc(0), in = make_idesc(1);
-    const uint32_t l0r = tmem + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
-    for (long long i = 0; i < my_tiles && __all_sync(0xffffffffu, ok); ++i) {
-      const int b = (int)(i & 1);
-      const uint32_t k = (uint32_t)(i >> 1);
-      ok = wait_bar(mbase + kBarFull + 8 * b, k & 1, abort, status);
+    for (long long i = 0; i < my_tiles; ++i) {
+      // box c of tile i is load number g = 4 i + c, in ring slot g mod 6
+      const long long g0 = 4 * i;
+      const int s0 = (int)(g0 % kSlots);
+      auto slot = [s0](int c) { return s0 + c >= kSlots ? s0 + c - kSlots : s0 + c; };
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long g = g0 + c;
+        if (ok) ok = wait_bar(mbase + kBarFull + 8 * slot(c), (uint32_t)((g / kSlots) & 1), abort,
+                              status);
+      }
       if (__any_sync(0xffffffffu, !ok)) break;  // the warp leaves together
-      const uint8_t* stage = smem + kOffStage + b * kStageBytes;
       // the row (64 complex) into registers; exponent 2^e >= max |x|
       float4 row[32];
       float m = 0.f;
 #pragma unroll
       for (int q = 0; q < 32; ++q) {
-        row[q] = *reinterpret_cast<const float4*>(stage + (q >> 3) * kBoxBytes + r * 128 +
-                                                  (((q & 7) ^ (r & 7)) << 4));
+        row[q] = *reinterpret_cast<const float4*>(smem + kOffRing + slot(q >> 3) * kBoxBytes +
+                                                  r * 128 + (((q & 7) ^ (r & 7)) << 4));
         m = fmaxf(m, fmaxf(fmaxf(fabsf(row[q].x), fabsf(row[q].y)),
                            fmaxf(fabsf(row[q].z), fabsf(row[q].w))));
       }
-      // the stage is no longer needed: let the producer refill it now
-      mbar_arrive(mbase + kBarSFree + 8 * b);
-      if (leader && issued < my_tiles && issued == i + 2) {
-        ok = wait_bar(mbase + kBarSFree + 8 * b, k & 1, abort, status);
-        if (ok) load_tile(issued++);
-      }
+      // the slots are no longer needed: let the producer refill them now
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
       int e = 0;
       if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
       const float scale = ldexpf(1.f, 7 - e);
@@ -404,104 +393,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(mbase + kBarAReady + 8 * h);
       }
       if (__any_sync(0xffffffffu, !ok)) break;
-      if (leader) {
-        // the MMAs of tile i once both halves of A are written and the
-        // epilogue has read out tile i - 1
-        for (int h = 0; h < 2 && ok; ++h)
-          ok = wait_bar(mbase + kBarAReady + 8 * h, (uint32_t)(i & 1), abort, status);
-        if (ok && i >= 1) ok = wait_bar(mbase + kBarDFree, (uint32_t)((i - 1) & 1), abort, status);
-        if (ok) {
-          tc_fence_after();
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t ab = tmem + kAHalf * h;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              // global k-step 2h + ks (K = 16): two core matrices along K
-              const uint64_t ko = (uint64_t)((2 * (2 * h + ks) * 1024) >> 4);
-              const uint32_t acc = (h > 0 || ks > 0) ? 1u : 0u;
-              const uint32_t r0 = ab + kColR0 + 8 * ks, r1 = ab + kColR1 + 8 * ks,
-                             r2 = ab + kColR2 + 8 * ks;
-              const uint32_t i0 = ab + kColI0 + 8 * ks, i1 = ab + kColI1 + 8 * ks,
-                             i2 = ab + kColI2 + 8 * ks;
-              // level 0 (exact): s0 u0
-              mma_bf16(l0r, r0, dr0 + ko, ip, acc);
-              mma_bf16(l0r, i0, di0 + ko, in, 1);
-              mma_bf16(l0i, r0, di0 + ko, ip, acc);
-              mma_bf16(l0i, i0, dr0 + ko, ip, 1);
-              // rest: s0 u1 + s1 u0 + s0 u2 + s1 u1 + s2 u0
-              mma_bf16(rr_, r0, dr1 + ko, ip, acc);
-              mma_bf16(rr_, r1, dr0 + ko, ip, 1);
-              mma_bf16(rr_, r0, dr2 + ko, ip, 1);
-              mma_bf16(rr_, r1, dr1 + ko, ip, 1);
-              mma_bf16(rr_, r2, dr0 + ko, ip, 1);
-              mma_bf16(rr_, i0, di1 + ko, in, 1);
-              mma_bf16(rr_, i1, di0 + ko, in, 1);
-              mma_bf16(rr_, i0, di2 + ko, in, 1);
-              mma_bf16(rr_, i1, di1 + ko, in, 1);
-              mma_bf16(rr_, i2, di0 + ko, in, 1);
-              mma_bf16(ri_, r0, di1 + ko, ip, acc);
-              mma_bf16(ri_, r1, di0 + ko, ip, 1);
-              mma_bf16(ri_, r0, di2 + ko, ip, 1);
-              mma_bf16(ri_, r1, di1 + ko, ip, 1);
-              mma_bf16(ri_, r2, di0 + ko, ip, 1);
-              mma_bf16(ri_, i0, dr1 + ko, ip, 1);
-              mma_bf16(ri_, i1, dr0 + ko, ip, 1);
-              mma_bf16(ri_, i0, dr2 + ko, ip, 1);
-              mma_bf16(ri_, i1, dr1 + ko, ip, 1);
-              mma_bf16(ri_, i2, dr0 + ko, ip, 1);
-            }
-            mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
-          }
-          mma_commit(mbase + kBarDFull);
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0) && ok;
     }
-    if (leader) {
-      // drain loads nobody will consume (abort path) before the CTA exits
-      for (long long i = issued - 2 < 0 ? 0 : issued - 2; i < issued && *abort; ++i) {
-        const long long t0 = clock64();
-        while (!mbar_try_wait(mbase + kBarFull + 8 * (int)(i & 1), (uint32_t)((i >> 1) & 1)) &&
-               clock64() - t0 < kTimeoutCycles) {
-        }
-      }
-      // all issued MMAs complete before TMEM is released
-      mma_commit(mbase + kBarMmaDone);
-      const long long t0 = clock64();
-      while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
-      }
-    }
-  } else {
+  } else if (wg == 1) {
     // ------------------------------------------------------------ epilogue
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
     const int q = warp - 4;
     const int r = q * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-    uint32_t yrow = 0;  // output-tile bits contributed by this row's bits
+    const bool elected = q == 0 && lane == 0;  // issues the tile's TMA store
+    // Output tile bits: row bit b of this tile goes to output bit sigma[6+b],
+    // window bit j to sigma[j]; output bits 0-5 are the next window (the
+    // contiguous 64 amplitudes), bits 6-12 the next rows.  The staging tile
+    // holds amplitude y at byte swz128(8 y), so the place of this row's
+    // element c is row_off ^ (XOR over set bits j of c of col_off[j]).
+    uint32_t yrow = 0;
     for (int bq = 0; bq < 7; ++bq) yrow |= ((uint32_t)(r >> bq) & 1u) << pa.sigma[kN + bq];
-    // Staging place of output element (ro, co) within its round:
-    // (ro & 63) * kOutRowStride + 8 co.  The relabel is a bit permutation, so
-    // the place of this row's element c is base + sum over set bits j of c of
-    // off[j], and its round (output bit 12) is bit c of a 64-bit mask.
-    const uint32_t base = ((yrow >> kN) & 63) * kOutRowStride + (yrow & (kCols - 1)) * 8;
-    uint32_t off[kN];
-    uint64_t round1 = 0;  // bit c: element c belongs to round 1
+    const uint32_t row_off = swz128(8u * yrow);
+    uint32_t col_off[kN];
 #pragma unroll
-    for (int j = 0; j < kN; ++j) {
-      const int sj = pa.sigma[j];
-      off[j] = sj < kN ? (8u << sj) : (sj < kN + 6 ? (kOutRowStride << (sj - kN)) : 0u);
-    }
-    for (int c = 0; c < kCols; ++c) {
-      uint32_t yo = yrow;
-      for (int j = 0; j < kN; ++j)
-        if ((c >> j) & 1) yo |= 1u << pa.sigma[j];
-      round1 |= (uint64_t)((yo >> 12) & 1u) << c;
-    }
-    float2* const psi_g = static_cast<float2*>(pa.psi);
+    for (int j = 0; j < kN; ++j) col_off[j] = swz128(8u << pa.sigma[j]);
+    const uint32_t out_base = sbase + kOffOut;
     Diag<float> dg;
     if (pa.diag) dg.init(pa.ep, pa.L);
     const float sc = (float)renorm_scale(pa.ep.rn);
     double eacc = 0.0, nacc = 0.0;
-    uint8_t* out = smem + kOffOut;
     for (long long i = 0; i < my_tiles; ++i) {
       const bool ok = wait_bar(mbase + kBarDFull, (uint32_t)(i & 1), abort, status);
       if (!epilogue_all_ok(ok)) break;  // the four epilogue warps leave together
@@ -537,50 +452,49 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       const long long t = blockIdx.x + i * gridDim.x;
-      const uint64_t tlo = (uint64_t)t & ((1ull << (a - kN)) - 1);
-      const uint64_t thi = (uint64_t)t >> (a - kN);
-      const uint64_t tbase = (tlo << kN) | (thi << (a + 7));
-      // The relabelled tile leaves in two rounds of 64 output rows: scatter
-      // this row's amplitudes to their output places in the staging buffer,
-      // then copy whole output rows to global memory with coalesced 16-byte
-      // stores.
-#pragma unroll 1
-      for (int round = 0; round < 2; ++round) {
-        // offsets are recomputed per round rather than kept live (registers)
-#pragma unroll
-        for (int j = 0; j < kN; ++j) asm volatile("" : "+r"(off[j]));
-        const uint64_t want = round ? round1 : ~round1;
+      const uint32_t tlo = (uint32_t)(t & ((1ll << (a - kN)) - 1));
+      const uint32_t thi = (uint32_t)(t >> (a - kN));
+      if (pa.diag) {
+        // the period's last pass writes the natural layout: measure the
+        // diagonal part and the norm on the amplitudes' natural indices
+        const uint64_t tbase = ((uint64_t)tlo << kN) | ((uint64_t)thi << (a + 7));
 #pragma unroll
         for (int c = 0; c < kCols; ++c) {
-          uint32_t o = base;
+          uint32_t yo = yrow;
 #pragma unroll
-          for (int j = 0; j < kN; ++j)
-            if ((c >> j) & 1) o += off[j];
-          if ((want >> c) & 1) *reinterpret_cast<float2*>(out + o) = make_float2(re[c], im[c]);
+          for (int j = 0; j < kN; ++j) yo |= (uint32_t)((c >> j) & 1) << pa.sigma[j];
+          const uint64_t x = tbase | (yo & (kCols - 1)) | ((uint64_t)(yo >> kN) << a);
+          const float p = re[c] * re[c] + im[c] * im[c];
+          ns += p;
+          es += p * dg(x);
         }
-        epilogue_sync();
-        // warp q copies output rows [16 q, 16 q + 16) of this round
-#pragma unroll 4
-        for (int k2 = 0; k2 < 16; ++k2) {
-          const uint32_t rr = 16 * q + k2;
-          const uint8_t* src = out + rr * kOutRowStride + 16 * lane;
-          const float2 lo = *reinterpret_cast<const float2*>(src);
-          const float2 hi = *reinterpret_cast<const float2*>(src + 8);
-          const float4 v = make_float4(lo.x, lo.y, hi.x, hi.y);
-          const uint64_t ro = 64 * round + rr;
-          const uint64_t x = tbase + (ro << a) + 2 * lane;  // natural index of (ro, 2 lane)
-          *reinterpret_cast<float4*>(psi_g + x) = v;
-          if (pa.diag) {
-            const float p0 = v.x * v.x + v.y * v.y, p1 = v.z * v.z + v.w * v.w;
-            ns += p0 + p1;
-            es += p0 * dg(x) + p1 * dg(x + 1);
-          }
-        }
-        epilogue_sync();  // the staging buffer may be refilled
       }
       eacc += (double)es;
       nacc += (double)ns;
+      // the staging tile is free once the previous tile's store has read it
+      if (elected) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      epilogue_sync();
+      // Relabelled write of the row, visiting c in Gray-code order so that
+      // one XOR moves the place from one element to the next; the 32 lanes
+      // of a store differ in row bits only.
+      uint32_t o = row_off;
+#pragma unroll
+      for (int g = 0; g < kCols; ++g) {
+        const int c = g ^ (g >> 1);
+        if (g > 0) o ^= col_off[low_bit(g)];
+        asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(out_base + o), "f"(re[c]),
+                     "f"(im[c])
+                     : "memory");
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      epilogue_sync();
+      if (elected) {
+        tma_store_3d(&tmap_out, out_base, 0, (int)(tlo << 2), (int)(thi << 7));
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
     }
+    // the CTA's stores complete before its shared memory is released
+    if (elected) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     // energy partials of this CTA (fixed order)
     if (pa.partial) {
 #pragma unroll
@@ -597,6 +511,112 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (q == 0 && lane == 0) {
         pa.partial[2 * blockIdx.x] = (red[0] + red[2]) + (red[4] + red[6]);
         pa.partial[2 * blockIdx.x + 1] = (red[1] + red[3]) + (red[5] + red[7]);
+      }
+    }
+  } else {
+    // ----------------------------------- MMA issue (warp 8), producer (warp 9)
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
+    const uint32_t w0 = sbase + kOffW;
+    if (warp == 8 && lane == 0) {
+      const uint64_t dr0 = make_desc(w0), dr1 = make_desc(w0 + kMatBytes),
+                     dr2 = make_desc(w0 + 2 * kMatBytes), di0 = make_desc(w0 + 3 * kMatBytes),
+                     di1 = make_desc(w0 + 4 * kMatBytes), di2 = make_desc(w0 + 5 * kMatBytes);
+      constexpr uint32_t ip = make_idesc(0), in = make_idesc(1);
+      const uint32_t l0r = tmem + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
+      bool ok = wait_bar(mbase + kBarW, 0, abort, status);
+      for (long long i = 0; i < my_tiles && ok; ++i) {
+        for (int h = 0; h < 2 && ok; ++h) {
+          // half h of tile i once its A digits are written and, for the first
+          // half, once the epilogue has read out tile i - 1
+          ok = wait_bar(mbase + kBarAReady + 8 * h, (uint32_t)(i & 1), abort, status);
+          if (ok && h == 0 && i >= 1)
+            ok = wait_bar(mbase + kBarDFree, (uint32_t)((i - 1) & 1), abort, status);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t ab = tmem + kAHalf * h;
+#pragma unroll 1
+          for (int ks = 0; ks < 2; ++ks) {
+            // global k-step 2h + ks (K = 16): two core matrices along K
+            const uint64_t ko = (uint64_t)((2 * (2 * h + ks) * 1024) >> 4);
+            const uint32_t acc = (h > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t r0 = ab + kColR0 + 8 * ks, r1 = ab + kColR1 + 8 * ks,
+                           r2 = ab + kColR2 + 8 * ks;
+            const uint32_t i0 = ab + kColI0 + 8 * ks, i1 = ab + kColI1 + 8 * ks,
+                           i2 = ab + kColI2 + 8 * ks;
+            // level 0 (exact): s0 u0
+            mma_bf16(l0r, r0, dr0 + ko, ip, acc);
+            mma_bf16(l0r, i0, di0 + ko, in, 1);
+            mma_bf16(l0i, r0, di0 + ko, ip, acc);
+            mma_bf16(l0i, i0, dr0 + ko, ip, 1);
+            // rest: s0 u1 + s1 u0 + s0 u2 + s1 u1 + s2 u0
+            mma_bf16(rr_, r0, dr1 + ko, ip, acc);
+            mma_bf16(rr_, r1, dr0 + ko, ip, 1);
+            mma_bf16(rr_, r0, dr2 + ko, ip, 1);
+            mma_bf16(rr_, r1, dr1 + ko, ip, 1);
+            mma_bf16(rr_, r2, dr0 + ko, ip, 1);
+            mma_bf16(rr_, i0, di1 + ko, in, 1);
+            mma_bf16(rr_, i1, di0 + ko, in, 1);
+            mma_bf16(rr_, i0, di2 + ko, in, 1);
+            mma_bf16(rr_, i1, di1 + ko, in, 1);
+            mma_bf16(rr_, i2, di0 + ko, in, 1);
+            mma_bf16(ri_, r0, di1 + ko, ip, acc);
+            mma_bf16(ri_, r1, di0 + ko, ip, 1);
+            mma_bf16(ri_, r0, di2 + ko, ip, 1);
+            mma_bf16(ri_, r1, di1 + ko, ip, 1);
+            mma_bf16(ri_, r2, di0 + ko, ip, 1);
+            mma_bf16(ri_, i0, dr1 + ko, ip, 1);
+            mma_bf16(ri_, i1, dr0 + ko, ip, 1);
+            mma_bf16(ri_, i0, dr2 + ko, ip, 1);
+            mma_bf16(ri_, i1, dr1 + ko, ip, 1);
+            mma_bf16(ri_, i2, dr0 + ko, ip, 1);
+          }
+          mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
+        }
+        if (ok) mma_commit(mbase + kBarDFull);
+      }
+      // all issued MMAs complete before TMEM is released
+      mma_commit(mbase + kBarMmaDone);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
+      }
+    } else if (warp == 9 && lane == 0) {
+      // load number g is box (g mod 4) of tile g / 4, into slot g mod 6
+      auto load_box = [&](long long g) {
+        const long long t = blockIdx.x + (g >> 2) * gridDim.x;
+        const int tlo = (int)(t & ((1ll << (a - kN)) - 1));
+        const int thi = (int)(t >> (a - kN));
+        const int slot = (int)(g % kSlots);
+        const uint32_t bar = mbase + kBarFull + 8 * slot;
+        mbar_expect_tx(bar, kBoxBytes);
+        tma_load_5d(sbase + kOffRing + slot * kBoxBytes, &tmap_in, bar, 0, (int)(g & 3), tlo, 0,
+                    thi);
+      };
+      mbar_expect_tx(mbase + kBarW, kWBytes);
+      const uint8_t* wsrc = static_cast<const uint8_t*>(pa.W);
+      for (int q = 0; q < 3; ++q)
+        bulk_load(w0 + q * (kWBytes / 3), wsrc + q * (kWBytes / 3), kWBytes / 3, mbase + kBarW);
+      const long long nloads = 4 * my_tiles;
+      long long issued = 0;
+      for (; issued < nloads; ++issued) {
+        // a slot is reused once the converters have read its previous box
+        if (issued >= kSlots &&
+            !wait_bar(mbase + kBarEmpty + 8 * (int)(issued % kSlots),
+                      (uint32_t)((issued / kSlots - 1) & 1), abort, status))
+          break;
+        load_box(issued);
+      }
+      if (*abort) {
+        // drain copies nobody will consume before the CTA exits
+        for (long long g = issued - kSlots < 0 ? 0 : issued - kSlots; g < issued; ++g) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(mbase + kBarFull + 8 * (int)(g % kSlots),
+                                (uint32_t)((g / kSlots) & 1)) &&
+                 clock64() - t0 < kTimeoutCycles) {
+          }
+        }
+        const long long t0 = clock64();
+        while (!mbar_try_wait(mbase + kBarW, 0) && clock64() - t0 < kTimeoutCycles) {
+        }
       }
     }
   }
@@ -670,22 +690,37 @@ void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out
   std::memcpy(out.data(), h.data(), kWBytes);
 }
 
+// Two descriptors per pass: the load view (tile rows as 128-row boxes of
+// 128 bytes: window amplitudes 16 c .. 16 c + 15 of each row) and the store
+// view (the staging tile's output order: amplitudes 0-15 of an output row,
+// output bits 4-5 joined with the tile bits below the row bits, output row
+// bits 6-12 joined with the tile bits above them).
 int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return SV_ECUDA;
   const int a = pa.a, L = pa.L;
+  alignas(64) CUtensorMap maps[2];
   cuuint64_t dims[5] = {32, 4, (cuuint64_t)1 << (a - kN), 128, (cuuint64_t)1 << (L - a - 7)};
   cuuint64_t strides[4] = {128, 512, (cuuint64_t)8 << a, (cuuint64_t)8 << (a + 7)};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   cuuint32_t box_in[5] = {32, 1, 1, 128, 1};
-  CUresult rc = fn(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, psi,
-                   dims, strides, box_in, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return rc == CUDA_SUCCESS ? SV_OK : SV_ECUDA;
+  CUresult rc = fn(&maps[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, psi, dims, strides, box_in,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (rc != CUDA_SUCCESS) return SV_ECUDA;
+  // store view: 8-byte elements (one complex amplitude each)
+  cuuint64_t odims[3] = {16, (cuuint64_t)1 << (a - 4), (cuuint64_t)1 << (L - a)};
+  cuuint64_t ostrides[2] = {128, (cuuint64_t)8 << a};
+  cuuint32_t obox[3] = {16, 4, 128};
+  rc = fn(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, psi, odims, ostrides, obox, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (rc != CUDA_SUCCESS) return SV_ECUDA;
+  std::memcpy(map_out, maps, sizeof(maps));  // the caller's buffer need not be aligned
+  return SV_OK;
 }
 
-size_t block_tc_map_bytes() { return sizeof(CUtensorMap); }
+size_t block_tc_map_bytes() { return 2 * sizeof(CUtensorMap); }
 
 cudaError_t block_tc_prepare() {
   return cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -696,8 +731,9 @@ cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int*
                             int grid, cudaStream_t s) {
   PassArgs p = pa;
   p.psi = psi;
-  k_block_tc<<<grid, kThreads, kSmemBytes, s>>>(*static_cast<const CUtensorMap*>(map), p,
-                                                status);
+  alignas(64) CUtensorMap maps[2];
+  std::memcpy(maps, map, sizeof(maps));
+  k_block_tc<<<grid, kThreads, kSmemBytes, s>>>(maps[0], maps[1], p, status);
   return cudaGetLastError();
 }
 

@@ -57,10 +57,13 @@ def test_tensor_core_block_form_matches_oracle(svlib, L):
     cores) against the oracle, element by element and in energy."""
     cfg = inputs.ChainConfig(L=L, periods=3, seed=80 + L)
     psi_o, _, e_o, n_o = orc.run_chain(cfg)
-    e, nn, psi, _ = _run_block(cfg, 6, capi.SV_SPLIT_BF16X3, cfg.periods, expect_tc=True)
+    e, nn, psi, info = _run_block(cfg, 6, capi.SV_SPLIT_BF16X3, cfg.periods, expect_tc=True)
     assert _infidelity(psi, psi_o) < 1e-8
+    # Each pass rounds the state to 2^-23 of every row's largest amplitude
+    # (one exponent per row of 64): up to ~1e-6 of the state norm per pass,
+    # accumulating as a random walk over the passes.
     err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
-    assert err < 1e-5, err
+    assert err < 4e-6 * np.sqrt(cfg.periods * info[0]), err
     np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
     np.testing.assert_allclose(nn, n_o, atol=5e-6, rtol=0)
 

@@ -36,8 +36,9 @@
 //               tile kept in the output's own order under the 128-byte
 //               swizzle (one XOR per amplitude, visiting the row in Gray-code
 //               order), and one TMA tensor store writes the tile back.
-//   warp 8      one thread issues the 96 MMAs of each tile (M=128, N=64,
-//               K=16, A in TMEM, B in shared memory), half by half.
+//   warp 8      issues the 96 MMAs of each tile (M=128, N=64, K=16, A in
+//               TMEM, B in shared memory), half by half, from one elected
+//               lane of the converged warp.
 //   warp 9      one thread keeps the TMA producer going: the pass's six
 //               64x64 bf16 digit matrices once, then four 128-row x 128-byte
 //               boxes per tile (cp.async.bulk.tensor.5d, 128-byte swizzle)
@@ -240,27 +241,42 @@ __host__ __device__ constexpr uint32_t make_idesc(int negate_b) {
          ((uint32_t)(kCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 }
 
+// Issued by one elected lane while the whole warp runs the issue loop: the
+// operands are then warp-uniform and the MMAs go out at the tensor pipe's
+// rate (an N = 64 MMA every 32 cycles, against about 50 for a lone lane).
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
       "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
+// tcgen05.commit from one elected lane of a converged warp
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+          bar)
       : "memory");
 }
 
-// Two values with at most 8 significant bits each (exact in bf16), packed
-// as bf16x2 with `lo` in the low half.
+// Two values with at most 8 significant bits each, packed as bf16x2 with
+// `lo` in the low half: their FP32 encodings end in 16 zero bits, so the
+// bf16 values are the high halves (a byte permute, no rounding).
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  uint32_t d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
-  return d;
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// Rounding to a multiple of 2^(Q-23) with the FP32 adder: for
+// |v| < 2^(Q-1), (v + 1.5*2^Q) - 1.5*2^Q is v rounded to nearest (ties to
+// even) at the unit 2^(Q-23).  Both additions are exact apart from that
+// one rounding.
+template <int Q>
+__device__ __forceinline__ float round_at(float v) {
+  constexpr float kM = 1.5f * (float)(1ull << Q);
+  return __fsub_rn(__fadd_rn(v, kM), kM);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -367,11 +383,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             float d0[4], d1[4], d2[4];
 #pragma unroll
             for (int e2 = 0; e2 < 4; ++e2) {
-              d0[e2] = rintf(y[e2]);
-              const float t1 = (y[e2] - d0[e2]) * 256.f;  // exact
-              d1[e2] = rintf(t1);
-              d2[e2] = rintf((t1 - d1[e2]) * 256.f) * (1.f / 65536.f);
-              d1[e2] *= (1.f / 256.f);  // digits as d, d/256, d/65536: exact bf16
+              // digits at their own scale: d0 integer, d1 a multiple of
+              // 2^-8, d2 of 2^-16, each at most 128 units (8 bits, exact in
+              // bf16); the remainders are exact
+              d0[e2] = round_at<23>(y[e2]);
+              const float r1 = __fsub_rn(y[e2], d0[e2]);
+              d1[e2] = round_at<15>(r1);
+              d2[e2] = round_at<7>(__fsub_rn(r1, d1[e2]));
             }
             r0[s] = pack_bf16x2(d0[0], d0[2]);
             i0[s] = pack_bf16x2(d0[1], d0[3]);
@@ -517,24 +535,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ----------------------------------- MMA issue (warp 8), producer (warp 9)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
     const uint32_t w0 = sbase + kOffW;
-    if (warp == 8 && lane == 0) {
+    if (warp == 8) {
+      // the whole warp runs this loop; mma_bf16 / mma_commit issue from one lane
+      const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
       const uint64_t dr0 = make_desc(w0), dr1 = make_desc(w0 + kMatBytes),
                      dr2 = make_desc(w0 + 2 * kMatBytes), di0 = make_desc(w0 + 3 * kMatBytes),
                      di1 = make_desc(w0 + 4 * kMatBytes), di2 = make_desc(w0 + 5 * kMatBytes);
       constexpr uint32_t ip = make_idesc(0), in = make_idesc(1);
-      const uint32_t l0r = tmem + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
-      bool ok = wait_bar(mbase + kBarW, 0, abort, status);
+      const uint32_t l0r = tm + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
+      bool ok = __all_sync(0xffffffffu, wait_bar(mbase + kBarW, 0, abort, status));
       for (long long i = 0; i < my_tiles && ok; ++i) {
+#pragma unroll 1
         for (int h = 0; h < 2 && ok; ++h) {
           // half h of tile i once its A digits are written and, for the first
           // half, once the epilogue has read out tile i - 1
           ok = wait_bar(mbase + kBarAReady + 8 * h, (uint32_t)(i & 1), abort, status);
           if (ok && h == 0 && i >= 1)
             ok = wait_bar(mbase + kBarDFree, (uint32_t)((i - 1) & 1), abort, status);
+          ok = __all_sync(0xffffffffu, ok);  // the warp stays converged
           if (!ok) break;
           tc_fence_after();
-          const uint32_t ab = tmem + kAHalf * h;
-#pragma unroll 1
+          const uint32_t ab = tm + kAHalf * h;
+#pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             // global k-step 2h + ks (K = 16): two core matrices along K
             const uint64_t ko = (uint64_t)((2 * (2 * h + ks) * 1024) >> 4);

@@ -6,21 +6,21 @@
 // when it aligns products and when it adds to D, which biases a long
 // evolution (measured: a dissipative drift of the energy density).  The
 // full-magnitude part of the product is therefore accumulated exactly:
-//   - each state row (64 complex = 128 reals) is scaled by a power of two
-//     2^(7-e_r) with 2^e_r >= max |x| and cut into three balanced 8-bit
-//     digits, x = 2^(e_r-7) (s0 + s1/256 + s2/65536), |s| <= 128, each
-//     rounded to nearest (the residual is below 2^-24 of the row's largest
-//     entry, as for FP32 rounding);
+//   - each state row (64 complex = 128 reals) with 2^e_r >= max |x| is cut
+//     into three balanced 8-bit digits at the row's own units,
+//     x = 2^(e_r-7) (s0 + s1/256 + s2/65536), |s| <= 128, each rounded to
+//     nearest (the residual is below 2^-24 of the row's largest entry, as
+//     for FP32 rounding);
 //   - each entry of the fused unitary likewise, u = 2^-7 (u0 + u1/256 +
 //     u2/65536);
-//   - digits are bf16 values d, d/256, d/65536 (exact), so s0 u0 products
-//     are integers below 2^14 and their sum over K = 64 (both complex parts)
-//     stays below 2^21: the level-0 accumulator is EXACT; all other products
-//     (s0u1, s1u0, s0u2, s1u1, s2u0) are at most 2^-8 of the total and go to
-//     a second accumulator, whose truncation is 2^-8 smaller relative to the
-//     result (kind::f16 with bf16 inputs, FP32 accumulators in TMEM);
-//   - the epilogue adds the two with round-to-nearest FP32 arithmetic,
-//     out = 2^(e_r - 14) (L0 + R).
+//   - the digits are held as exact bf16 values at their true scale, so the
+//     s0 u0 products are integers below 2^14 in units of 2^(e_r-14), and
+//     their sum over K = 64 (both complex parts) stays below 2^21 units:
+//     the level-0 accumulator is EXACT; all other products (s0u1, s1u0,
+//     s0u2, s1u1, s2u0) are at most 2^-8 of the total and go to a second
+//     accumulator, whose truncation is 2^-8 smaller relative to the result
+//     (kind::f16 with bf16 inputs, FP32 accumulators in TMEM);
+//   - the epilogue adds the two with round-to-nearest FP32 arithmetic.
 //
 // Per CTA (one per SM, persistent over tiles), three warpgroups whose
 // register shares are rebalanced with setmaxnreg (168 a thread at launch,
@@ -102,7 +102,6 @@ enum : uint32_t {
   kTmemSlot = 160,
   kAbort = 164,
   kRed = 256,        // 4 x 2 doubles
-  kExp = 512,        // 2 x 128 int: row exponents per tile parity
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -269,14 +268,37 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// Rounding to a multiple of 2^(Q-23) with the FP32 adder: for
-// |v| < 2^(Q-1), (v + 1.5*2^Q) - 1.5*2^Q is v rounded to nearest (ties to
-// even) at the unit 2^(Q-23).  Both additions are exact apart from that
-// one rounding.
-template <int Q>
-__device__ __forceinline__ float round_at(float v) {
-  constexpr float kM = 1.5f * (float)(1ull << Q);
-  return __fsub_rn(__fadd_rn(v, kM), kM);
+// Packed FP32 pairs (two lanes per instruction on the FP32 pipe).
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Rounding with the FP32 adder: for |v| < 2^(q-1), (v + M) - M with
+// M = 1.5 * 2^q is v rounded to nearest (ties to even) at the unit
+// 2^(q-23); both additions are exact apart from that one rounding.
+__device__ __forceinline__ uint64_t round_at2(uint64_t v, uint64_t m) { return sub2(add2(v, m), m); }
+// 1.5 * 2^q as a float, for -126 < q < 128
+__device__ __forceinline__ float magic(int q) {
+  return __uint_as_float(((uint32_t)(q + 127) << 23) | 0x400000u);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -289,7 +311,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* misc = smem + kOffMisc;
   const uint32_t mbase = sbase + kOffMisc;
   volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(misc + kAbort);
-  int* row_exp = reinterpret_cast<int*>(misc + kExp);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = pa.a;
   const long long ntiles = pa.ntiles;
@@ -356,9 +377,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       // the slots are no longer needed: let the producer refill them now
 #pragma unroll
       for (int c = 0; c < 4; ++c) mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
-      int e = 0;
-      if (m > 0.f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
-      const float scale = ldexpf(1.f, 7 - e);
+      // 2^e >= max |x| (m = f 2^e, f in [0.5, 1)); rows below 2^-100 are
+      // cut at that unit (their digits stay normal bf16 numbers)
+      int e = -100;
+      if (m > 0x1p-100f) frexpf(m, &e);
+      // digit units 2^(e-7), 2^(e-15), 2^(e-23)
+      const uint64_t M0 = f2(magic(e + 16), magic(e + 16)), M1 = f2(magic(e + 8), magic(e + 8)),
+                     M2 = f2(magic(e), magic(e));
       for (int h = 0; h < 2 && ok; ++h) {
         if (i >= 1)
           ok = wait_bar(mbase + kBarAFree + 8 * h, (uint32_t)((i - 1) & 1), abort, status);
@@ -367,10 +392,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        // The exponent slot of this tile parity was last read by the epilogue
-        // of tile i - 2, before it released the accumulators for tile i - 1;
-        // A's first half being free for tile i means tile i - 1's MMAs ran.
-        if (h == 0) row_exp[(i & 1) * kRows + r] = e;
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
           const int c = 2 * h + cc;  // 16-amplitude chunk, k in [16 c, 16 c + 16)
@@ -379,17 +400,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int s = 0; s < 8; ++s) {
             const float4 v = row[8 * c + s];
             // amplitudes k = 16c + 2s and 16c + 2s + 1: (v.x, v.y), (v.z, v.w)
-            const float y[4] = {v.x * scale, v.y * scale, v.z * scale, v.w * scale};
-            float d0[4], d1[4], d2[4];
+            const uint64_t p[2] = {f2(v.x, v.y), f2(v.z, v.w)};
+            float d0[4], d1[4], d2[4];  // re k, im k, re k+1, im k+1
 #pragma unroll
-            for (int e2 = 0; e2 < 4; ++e2) {
-              // digits at their own scale: d0 integer, d1 a multiple of
-              // 2^-8, d2 of 2^-16, each at most 128 units (8 bits, exact in
-              // bf16); the remainders are exact
-              d0[e2] = round_at<23>(y[e2]);
-              const float r1 = __fsub_rn(y[e2], d0[e2]);
-              d1[e2] = round_at<15>(r1);
-              d2[e2] = round_at<7>(__fsub_rn(r1, d1[e2]));
+            for (int t = 0; t < 2; ++t) {
+              // each digit at most 128 of its unit (8 bits, exact in bf16);
+              // the remainders are exact
+              const uint64_t a0 = round_at2(p[t], M0);
+              const uint64_t q1 = sub2(p[t], a0);
+              const uint64_t a1 = round_at2(q1, M1);
+              const uint64_t a2 = round_at2(sub2(q1, a1), M2);
+              f2_split(a0, d0[2 * t], d0[2 * t + 1]);
+              f2_split(a1, d1[2 * t], d1[2 * t + 1]);
+              f2_split(a2, d2[2 * t], d2[2 * t + 1]);
             }
             r0[s] = pack_bf16x2(d0[0], d0[2]);
             i0[s] = pack_bf16x2(d0[1], d0[3]);
@@ -434,12 +457,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     Diag<float> dg;
     if (pa.diag) dg.init(pa.ep, pa.L);
     const float sc = (float)renorm_scale(pa.ep.rn);
+    const uint64_t sc2 = f2(sc, sc);
     double eacc = 0.0, nacc = 0.0;
     for (long long i = 0; i < my_tiles; ++i) {
       const bool ok = wait_bar(mbase + kBarDFull, (uint32_t)(i & 1), abort, status);
       if (!epilogue_all_ok(ok)) break;  // the four epilogue warps leave together
       tc_fence_after();
-      const float rs = ldexpf(sc, row_exp[(i & 1) * kRows + r] - 14);
       float re[kCols], im[kCols];
       const uint32_t acc = lane_base + kColAcc;
 #pragma unroll
@@ -451,9 +474,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld16(acc + 192 + 16 * c4, w1);  // R im
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          re[16 * c4 + e] = (__uint_as_float(v0[e]) + __uint_as_float(v1[e])) * rs;
-          im[16 * c4 + e] = (__uint_as_float(w0[e]) + __uint_as_float(w1[e])) * rs;
+        for (int e = 0; e < 16; e += 2) {
+          const uint64_t sre = mul2(add2(f2(__uint_as_float(v0[e]), __uint_as_float(v0[e + 1])),
+                                         f2(__uint_as_float(v1[e]), __uint_as_float(v1[e + 1]))),
+                                    sc2);
+          const uint64_t sim = mul2(add2(f2(__uint_as_float(w0[e]), __uint_as_float(w0[e + 1])),
+                                         f2(__uint_as_float(w1[e]), __uint_as_float(w1[e + 1]))),
+                                    sc2);
+          f2_split(sre, re[16 * c4 + e], re[16 * c4 + e + 1]);
+          f2_split(sim, im[16 * c4 + e], im[16 * c4 + e + 1]);
         }
       }
       tc_fence_before();
@@ -685,7 +714,7 @@ size_t block_tc_w_bytes(int n) { return n == kN ? kWBytes : 0; }
 
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
   // six K-major 64 x 64 bf16 digit matrices Ur0, Ur1, Ur2, Ui0, Ui1, Ui2
-  // holding u0, u1/256, u2/65536 with u = 2^-7 (u0 + u1/256 + u2/65536),
+  // holding u0/128, u1/32768, u2/2^23 with u = 2^-7 (u0 + u1/256 + u2/65536),
   // |u_t| <= 128, in the core-matrix order
   // of make_desc: element (row j, col k) at halfword
   // ((k/8)*8 + j/8)*64 + (j%8)*8 + k%8
@@ -700,7 +729,7 @@ void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out
       const double parts[2] = {u.real(), u.imag()};
       for (int ri = 0; ri < 2; ++ri) {
         double y = parts[ri] * 128.0;
-        double scale = 1.0;
+        double scale = 1.0 / 128.0;  // digits at their true scale
         for (int q = 0; q < 3; ++q) {
           const double d = std::nearbyint(y);
           h[(size_t)(3 * ri + q) * m + w] = bf16_of_int(d, scale);

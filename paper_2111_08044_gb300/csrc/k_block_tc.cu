@@ -24,7 +24,7 @@
 //
 // Per CTA (one per SM, persistent over tiles), three warpgroups whose
 // register shares are rebalanced with setmaxnreg (168 a thread at launch,
-// 128 x (224 + 224 + 56) in total):
+// 128 x (216 + 232 + 56) in total):
 //   warps 0-3   converters: thread = row = TMEM lane; digits of the row into
 //               TMEM (tcgen05.st) as the A operand, in two K-halves so that
 //               the next tile's conversion overlaps the current tile's MMAs.
@@ -68,7 +68,7 @@ using namespace dev;
 constexpr int kN = 6;                 // window width
 constexpr int kCols = 1 << kN;        // complex amplitudes per row
 constexpr int kRows = 128;            // tile rows = MMA M = TMEM lanes
-constexpr int kThreads = 384;         // three warpgroups; registers 224 / 224 / 56 a thread
+constexpr int kThreads = 384;         // three warpgroups; registers 216 / 232 / 56 a thread
 constexpr uint32_t kTileBytes = kRows * kCols * 8;   // 64 KiB
 constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KiB (one 128-byte column box)
 constexpr int kSlots = 6;                             // input ring: 1.5 tiles of boxes
@@ -102,6 +102,7 @@ enum : uint32_t {
   kTmemSlot = 160,
   kAbort = 164,
   kRed = 256,        // 4 x 2 doubles
+  kDiagQ = 512,      // 64 floats: window-window bond part of the diagonal
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int wg = warp >> 2;
   if (wg == 0) {
     // ------------------------------------------------------------ converters
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 216;" ::: "memory");
     const int r = warp * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (wg == 1) {
     // ------------------------------------------------------------ epilogue
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 232;" ::: "memory");
     const int q = warp - 4;
     const int r = q * 32 + lane;  // tile row = TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -454,8 +455,27 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int j = 0; j < kN; ++j) col_off[j] = swz128(8u << pa.sigma[j]);
     const uint32_t out_base = sbase + kOffOut;
-    Diag<float> dg;
-    if (pa.diag) dg.init(pa.ep, pa.L);
+    // Diagonal part on the natural layout (the period's last pass), per
+    // amplitude h(x) = J sum_p z_p z_{p+1} + sum_p cz_p z_p, z = 1 - 2 x_p.
+    // Within a row only the output bits fed by window bits change with c:
+    // h(x_c) = h(x_0) + sum_j c_j lin_j + Q[c], where lin_j is the change of
+    // flipping window bit j alone (its field and its bonds to the fixed
+    // bits, window neighbours counted at 0) and Q[c] = 4 J sum over adjacent
+    // window pairs of c_j c_k, a 64-entry table shared by all rows.
+    float* diag_q = reinterpret_cast<float*>(misc + kDiagQ);
+    // global bit of window bit j in the output
+    auto gcol = [&](int j) { return pa.sigma[j] < kN ? pa.sigma[j] : a + pa.sigma[j] - kN; };
+    if (pa.diag) {
+      if (r < kCols) {
+        float qv = 0.f;
+        for (int j = 0; j < kN; ++j)
+          for (int k = j + 1; k < kN; ++k)
+            if (((r >> j) & 1) && ((r >> k) & 1) && (gcol(j) - gcol(k) == 1 || gcol(k) - gcol(j) == 1))
+              qv += 4.f * (float)pa.ep.J;
+        diag_q[r] = qv;
+      }
+      epilogue_sync();
+    }
     const float sc = (float)renorm_scale(pa.ep.rn);
     const uint64_t sc2 = f2(sc, sc);
     double eacc = 0.0, nacc = 0.0;
@@ -505,15 +525,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the period's last pass writes the natural layout: measure the
         // diagonal part and the norm on the amplitudes' natural indices
         const uint64_t tbase = ((uint64_t)tlo << kN) | ((uint64_t)thi << (a + 7));
+        const uint64_t x0 = tbase | (yrow & (kCols - 1)) | ((uint64_t)(yrow >> kN) << a);
+        Diag<float> dg;
+        dg.init(pa.ep, pa.L);
+        const float h0 = dg(x0);
+        float lin[kN];
 #pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-          uint32_t yo = yrow;
+        for (int j = 0; j < kN; ++j) {
+          const int g = gcol(j);
+          float nb = 0.f;  // sum of the neighbours' z at c = 0
+          if (g >= 1) nb += 1.f - 2.f * (float)((x0 >> (g - 1)) & 1);
+          if (g <= pa.L - 2) nb += 1.f - 2.f * (float)((x0 >> (g + 1)) & 1);
+          const float czg = g == 0 ? dg.cz_first : (g == pa.L - 1 ? dg.cz_last : dg.cz_bulk);
+          lin[j] = -2.f * (czg + dg.J * nb);
+        }
+        // Gray-code walk over c: one window bit flips per step
+        float hl = h0;
 #pragma unroll
-          for (int j = 0; j < kN; ++j) yo |= (uint32_t)((c >> j) & 1) << pa.sigma[j];
-          const uint64_t x = tbase | (yo & (kCols - 1)) | ((uint64_t)(yo >> kN) << a);
+        for (int g = 0; g < kCols; ++g) {
+          const int c = g ^ (g >> 1);
+          if (g > 0) {
+            const int j = low_bit(g);
+            hl += ((c >> j) & 1) ? lin[j] : -lin[j];
+          }
           const float p = re[c] * re[c] + im[c] * im[c];
           ns += p;
-          es += p * dg(x);
+          es += p * (hl + diag_q[c]);
         }
       }
       eacc += (double)es;

@@ -288,6 +288,11 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
   uint64_t d;
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
@@ -509,13 +514,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(mbase + kBarDFree);  // the accumulators may be overwritten
       float es = 0.f, ns = 0.f;
       if (pa.x_mask) {
+        // <X_j> part of the row: 2 sum over c with bit j clear of
+        // re_c re_c' + im_c im_c', c' = c + 2^j; for j >= 1 two neighbouring
+        // columns go through one packed FMA
 #pragma unroll
         for (int j = 0; j < kN; ++j) {
           if (!((pa.x_mask >> j) & 1)) continue;
-          float sj = 0.f;
+          float sj;
+          if (j == 0) {
+            float t0 = 0.f, t1 = 0.f;
 #pragma unroll
-          for (int c = 0; c < kCols; ++c) sj += re[c] * re[c ^ (1 << j)] + im[c] * im[c ^ (1 << j)];
-          es += pa.cx[j] * sj;
+            for (int c = 0; c < kCols; c += 2) {
+              t0 = fmaf(re[c], re[c + 1], t0);
+              t1 = fmaf(im[c], im[c + 1], t1);
+            }
+            sj = t0 + t1;
+          } else {
+            uint64_t acc = f2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < kCols; c += 2) {
+              if ((c >> j) & 1) continue;
+              const int c2 = c + (1 << j);
+              acc = fma2(f2(re[c], re[c + 1]), f2(re[c2], re[c2 + 1]), acc);
+              acc = fma2(f2(im[c], im[c + 1]), f2(im[c2], im[c2 + 1]), acc);
+            }
+            float lo, hi;
+            f2_split(acc, lo, hi);
+            sj = lo + hi;
+          }
+          es += 2.f * pa.cx[j] * sj;
         }
       }
       const long long t = blockIdx.x + i * gridDim.x;

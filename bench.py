@@ -225,6 +225,18 @@ def _oracle_periods_per_s(L_sample: int, periods: int, seed: int):
     return periods / dt * scale, dt
 
 
+# DRAM bytes (read + write) of one tensor-core block pass from an ncu
+# capture at L=26 (profiles/k_block_tc_L26.md), per launch; traffic scales
+# with the number of tiles, i.e. with 2^L.
+TC_TRAFFIC_L26 = 1012.3e6
+
+
+def _traffic(args):
+    if args.split != "bf16x3" or args.n != 6:
+        return None
+    return TC_TRAFFIC_L26 * 2.0 ** (args.L - 26)
+
+
 def _cpu_cores():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -304,7 +316,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs exceed L2 (8 GiB state per replica); no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak, "traffic": _traffic(args),
                      "kernel": "block pass (one fused unitary + relabel per launch)",
                      "peak_source": peak_src},
         "block": {k: block[k] for k in ("periods_per_s", "passes_per_period",

@@ -358,14 +358,19 @@ __global__ void __launch_bounds__(256) k_period_reduce(const double* __restrict_
 }
 
 // ------------------------------------------------------------ product state
+// psi_x = prod_i s_i[b_i(x)] as (low-site factor) x (high-site factor): the
+// low T sites come from a shared table; each warp owns chunks of 2^T
+// consecutive amplitudes and forms the chunk's high-site factor with a
+// shuffle butterfly (lane s holds the factor of high site s), so every
+// amplitude costs one complex multiply and the pass runs at write bandwidth.
+// Factors are formed in FP64 and rounded once to R.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_product_state(typename CT<R>::C* __restrict__ psi,
                                                             int L,
                                                             const double* __restrict__ sp) {
   using C = typename CT<R>::C;
-  // low sites 0..T-1 from a shared table, the rest per chunk, in FP64
-  constexpr int T = 8;
-  __shared__ double2 tab[1 << T];
+  constexpr int T = 10;
+  __shared__ C tab[1 << T];
   const int t = L < T ? L : T;
   for (int j = threadIdx.x; j < (1 << t); j += blockDim.x) {
     double re = 1.0, im = 0.0;
@@ -376,26 +381,41 @@ __global__ void __launch_bounds__(kThreads) k_product_state(typename CT<R>::C* _
       im = re * si + im * sr;
       re = nr;
     }
-    tab[j] = make_double2(re, im);
+    C v;
+    v.x = (R)re;
+    v.y = (R)im;
+    tab[j] = v;
   }
   __syncthreads();
-  const uint64_t nchunks = 1ull << (L - t);
-  const uint64_t csize = 1ull << t;
-  for (uint64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    double hr = 1.0, hi = 0.0;
-    for (int s = t; s < L; ++s) {
-      const int b = (int)((ch >> (s - t)) & 1);
-      const double sr = sp[4 * s + 2 * b], si = sp[4 * s + 2 * b + 1];
-      const double nr = hr * sr - hi * si;
-      hi = hr * si + hi * sr;
-      hr = nr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int nh = L - t;  // high sites, at most 24
+  const uint64_t nchunks = 1ull << nh;
+  const uint32_t csize = 1u << t;
+  for (uint64_t ch = (uint64_t)blockIdx.x * warps + warp; ch < nchunks;
+       ch += (uint64_t)gridDim.x * warps) {
+    double fr = 1.0, fi = 0.0;
+    if (lane < nh) {
+      const int b = (int)((ch >> lane) & 1);
+      fr = sp[4 * (t + lane) + 2 * b];
+      fi = sp[4 * (t + lane) + 2 * b + 1];
     }
-    for (uint64_t j = threadIdx.x; j < csize; j += blockDim.x) {
-      const double2 lo = tab[j];
-      C out;
-      out.x = (R)(hr * lo.x - hi * lo.y);
-      out.y = (R)(hr * lo.y + hi * lo.x);
-      psi[ch * csize + j] = out;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double gr = __shfl_xor_sync(0xffffffffu, fr, o);
+      const double gi = __shfl_xor_sync(0xffffffffu, fi, o);
+      const double nr = fr * gr - fi * gi;
+      fi = fr * gi + fi * gr;
+      fr = nr;
+    }
+    const R hr = (R)fr, hi = (R)fi;
+    C* __restrict__ out = psi + ch * csize;
+    for (uint32_t j = lane; j < csize; j += 32) {
+      const C lo = tab[j];
+      C v;
+      v.x = hr * lo.x - hi * lo.y;
+      v.y = hr * lo.y + hi * lo.x;
+      out[j] = v;
     }
   }
 }

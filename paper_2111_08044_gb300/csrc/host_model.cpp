@@ -261,6 +261,60 @@ std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
   return out;
 }
 
+std::vector<AdjOp> adjoint_period_ops(int L, const sv_floquet_params &p, double theta,
+                                      double hx) {
+  auto dagger4 = [](const cd *m, cd *out) {
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) out[4 * r + c] = std::conj(m[4 * c + r]);
+  };
+  std::vector<AdjOp> ops;
+  // kick: exp(-i theta X) on each site; d/dtheta R R^dagger = -i X
+  cd R[4], I2[4] = {1, 0, 0, 1}, X[4] = {0, 1, 1, 0}, mX[4], O[16], t1[16], t2[16];
+  kick_matrix(theta, R);
+  for (int k = 0; k < 4; ++k) mX[k] = -kI * X[k];
+  for (int i = 0; i + 1 < L; i += 2) {
+    AdjOp op;
+    op.bond = i;
+    op.kind = 0;
+    kron2(R, R, O);
+    dagger4(O, op.odag);
+    kron2(mX, I2, t1);
+    kron2(I2, mX, t2);
+    for (int k = 0; k < 16; ++k) op.d[k] = t1[k] + t2[k];
+    ops.push_back(op);
+  }
+  if (L % 2 == 1) {
+    AdjOp op;
+    op.bond = L - 2;
+    op.kind = 0;
+    kron2(I2, R, O);
+    dagger4(O, op.odag);
+    kron2(I2, mX, op.d);
+    ops.push_back(op);
+  }
+  // gates: G_b = exp(-i tau h_b(hx)), dh_b/dhx is h_b at J = hz = 0, hx = 1
+  const double tau = p.T / p.K;
+  std::vector<AdjOp> gate_ops(L - 1);
+  for (int b = 0; b < L - 1; ++b) {
+    cd h[16], dh[16], g[16], dg[16], gd[16];
+    bond_hamiltonian(L, b, p.J, hx, p.hz, p.edge_field_weight, h);
+    bond_hamiltonian(L, b, 0.0, 1.0, 0.0, p.edge_field_weight, dh);
+    expm_herm4_frechet(h, dh, tau, g, dg);
+    AdjOp &op = gate_ops[b];
+    op.bond = b;
+    op.kind = 1;
+    dagger4(g, gd);
+    std::memcpy(op.odag, gd, sizeof(gd));
+    matmul4(dg, gd, op.d);
+  }
+  for (int s = p.K - 1; s >= 0; --s)
+    for (int layer = 1; layer >= 0; --layer) {
+      const int parity = layer == 0 ? p.first_layer : 1 - p.first_layer;
+      for (int b = parity; b < L - 1; b += 2) ops.push_back(gate_ops[b]);
+    }
+  return ops;
+}
+
 Observable observable(int L, const sv_floquet_params &p) {
   Observable o;
   o.L = L;

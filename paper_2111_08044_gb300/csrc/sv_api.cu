@@ -673,11 +673,129 @@ int sv_renormalize(sv_ctx* ctx, double* norm2_before) {
 }
 
 int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_density) {
-  (void)grad_theta;
-  (void)grad_hx;
-  (void)energy_density;
-  if (!ctx) return SV_EINVAL;
-  return fail(ctx, SV_EUNSUPPORTED, "adjoint not built yet");
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (ctx->params.mode != SV_MODE_PLAIN)
+    return fail(ctx, SV_EUNSUPPORTED, "the adjoint needs SV_MODE_PLAIN");
+  if (ctx->n_period_params <= 0)
+    return fail(ctx, SV_ESTATE, "the adjoint needs per-period parameters (n_period_params > 0)");
+  if (ctx->counter != 0)
+    return fail(ctx, SV_ESTATE, "the adjoint starts at period 0 (counter is %lld)",
+                (long long)ctx->counter);
+  const int L = ctx->L;
+  const int64_t P = ctx->n_period_params;
+  const bool c128 = ctx->precision == SV_C128;
+  const size_t cb = amp_bytes(ctx->precision);
+  DeviceGuard dg(ctx->device);
+  // operation tables of every period, reverse order within a period
+  std::vector<std::vector<fsv::AdjOp>> ops((size_t)P);
+  for (int64_t k = 0; k < P; ++k)
+    ops[k] = fsv::adjoint_period_ops(L, ctx->params, ctx->theta_p[k], ctx->hx_p[k]);
+  const size_t nop = ops[0].size();
+  const size_t tab_elems = (size_t)P * nop * 32;  // odag, d per operation
+  std::vector<float2> tab32;
+  std::vector<double2> tab64;
+  if (c128)
+    tab64.resize(tab_elems);
+  else
+    tab32.resize(tab_elems);
+  for (int64_t k = 0; k < P; ++k)
+    for (size_t o = 0; o < nop; ++o) {
+      const fsv::AdjOp& op = ops[k][o];
+      const size_t at = ((size_t)k * nop + o) * 32;
+      if (c128) {
+        for (int e = 0; e < 16; ++e) {
+          tab64[at + e] = make_double2(op.odag[e].real(), op.odag[e].imag());
+          tab64[at + 16 + e] = make_double2(op.d[e].real(), op.d[e].imag());
+        }
+      } else {
+        round_unitary4(op.odag, &tab32[at]);
+        for (int e = 0; e < 16; ++e)
+          tab32[at + 16 + e] = make_float2((float)op.d[e].real(), (float)op.d[e].imag());
+      }
+    }
+  const int grid = fsv::adjoint_grid(ctx->cfg);
+  const size_t npart = nop * (size_t)grid;
+  void* d_lam = nullptr;
+  void* d_tab = nullptr;
+  double* d_part = nullptr;
+  double* d_grad = nullptr;
+  auto release = [&]() {
+    cudaFree(d_lam);
+    cudaFree(d_tab);
+    cudaFree(d_part);
+    cudaFree(d_grad);
+  };
+  if (cudaMalloc(&d_lam, cb << L) != cudaSuccess ||
+      cudaMalloc(&d_tab, tab_elems * (c128 ? sizeof(double2) : sizeof(float2))) != cudaSuccess ||
+      cudaMalloc(&d_part, sizeof(double) * npart) != cudaSuccess ||
+      cudaMalloc(&d_grad, sizeof(double) * (2 * (size_t)P + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(ctx, SV_ENOMEM, "adjoint buffers (%zu bytes for lambda)", cb << L);
+  }
+  auto run = [&]() -> int {
+    SV_CUDA(cudaMemcpyAsync(d_tab, c128 ? (const void*)tab64.data() : (const void*)tab32.data(),
+                            tab_elems * (c128 ? sizeof(double2) : sizeof(float2)),
+                            cudaMemcpyHostToDevice, ctx->stream),
+            "upload adjoint tables");
+    // forward to psi_P without storing states
+    int r = sv_evolve(ctx, P, nullptr, nullptr);
+    if (r) return r;
+    // seed lambda = (H0 / L) psi_P; f = Re <psi_P|lambda>
+    fsv::H0Coef h;
+    h.J = ctx->obs.J;
+    for (int i = 0; i < L; ++i) {
+      h.cx[i] = ctx->obs.cx[i];
+      h.cz[i] = ctx->obs.cz[i];
+    }
+    SV_CUDA(fsv::launch_apply_h0(ctx->precision, ctx->state, d_lam, L, h, d_part, ctx->cfg,
+                                 ctx->stream),
+            "adjoint seed launch");
+    SV_CUDA(fsv::launch_grad_reduce(d_part, grid, d_grad + 2 * P, 0, ctx->stream),
+            "energy reduce launch");
+    // reverse sweep: each operation's partials in its own slice, then the
+    // period's kick and drive slices summed in a fixed order
+    const size_t eb = c128 ? sizeof(double2) : sizeof(float2);
+    for (int64_t k = P - 1; k >= 0; --k) {
+      size_t nkick = 0;
+      for (size_t o = 0; o < nop; ++o) {
+        const fsv::AdjOp& op = ops[k][o];
+        if (op.kind == 0) ++nkick;
+        const char* base = static_cast<const char*>(d_tab) + ((size_t)k * nop + o) * 32 * eb;
+        SV_CUDA(fsv::launch_adjoint_gate(ctx->precision, ctx->state, d_lam, L, op.bond, base,
+                                         base + 16 * eb, d_part + o * (size_t)grid, ctx->cfg,
+                                         ctx->stream),
+                "adjoint gate launch");
+      }
+      // the kick operations come first in each period's list
+      SV_CUDA(fsv::launch_grad_reduce(d_part, (long long)(nkick * grid), d_grad + 2 * k, 1,
+                                      ctx->stream),
+              "gradient reduce launch");
+      SV_CUDA(fsv::launch_grad_reduce(d_part + nkick * grid, (long long)((nop - nkick) * grid),
+                                      d_grad + 2 * k + 1, 1, ctx->stream),
+              "gradient reduce launch");
+    }
+    std::vector<double> hg(2 * (size_t)P + 1);
+    SV_CUDA(cudaMemcpyAsync(hg.data(), d_grad, sizeof(double) * hg.size(),
+                            cudaMemcpyDeviceToHost, ctx->stream),
+            "gradient readback");
+    SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+    for (int64_t k = 0; k < P; ++k) {
+      if (grad_theta) grad_theta[k] = hg[2 * k];
+      if (grad_hx) grad_hx[k] = hg[2 * k + 1];
+    }
+    if (energy_density) *energy_density = hg[2 * P];
+    // psi is back at its starting point: so is the period counter
+    SV_CUDA(cudaMemsetAsync(ctx->d_counter, 0, sizeof(long long), ctx->stream),
+            "reset counter");
+    SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+    ctx->counter = 0;
+    return SV_OK;
+  };
+  rc = run();
+  release();
+  return rc;
 }
 
 int sv_get_state(sv_ctx* ctx, void* host_dst, size_t bytes) {

@@ -45,6 +45,22 @@ void expm_herm4_frechet(const cd h[16], const cd dh[16], double tau, cd g[16],
                         cd d[16]);
 // kick exp(-i theta X)
 void kick_matrix(double theta, cd r[4]);
+
+// One operation of the adjoint sweep: a two-site operator O on bond
+// (bond, bond+1), with O^dagger and D = (dO/dalpha) O^dagger for the
+// parameter alpha it depends on (kind 0: the kick angle theta_p, kind 1:
+// the drive field hx_p).
+struct AdjOp {
+  int bond = 0;
+  int kind = 0;
+  cd odag[16];
+  cd d[16];
+};
+// The operations of one period in the reverse of their order of
+// application: the kick (on site pairs (0,1), (2,3), ..., and site L-1
+// alone for odd L), then the gate layers from last to first.
+std::vector<AdjOp> adjoint_period_ops(int L, const sv_floquet_params &p, double theta,
+                                      double hx);
 // a1 + a2: the period's gates in application order with the kick folded
 // into the last gate on each site and epilogue flags set.
 std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,

@@ -64,4 +64,31 @@ cudaError_t launch_renormalize(int precision, void* psi, int L, const double* ri
                                int ring_len, const long long* counter,
                                const LaunchCfg& cfg, cudaStream_t s);
 
+// Coefficients of H0 = J sum_b Z_b Z_{b+1} + sum_i cx[i] X_i + sum_i cz[i] Z_i
+// (L <= 34), passed by value to the adjoint seed kernel.
+struct H0Coef {
+  double J = 0.0;
+  double cx[34] = {};
+  double cz[34] = {};
+};
+
+// Blocks of the adjoint kernels (also the number of partials each writes).
+int adjoint_grid(const LaunchCfg& cfg);
+
+// lambda = (H0 / L) psi; partial[block] = that block's share of
+// Re <psi|lambda>.
+cudaError_t launch_apply_h0(int precision, const void* psi, void* lam, int L, const H0Coef& h,
+                            double* partial, const LaunchCfg& cfg, cudaStream_t s);
+
+// One reverse step on bond (bond, bond+1): partial[block] = that block's
+// share of Re <lambda|D|psi>, then psi <- odag psi, lambda <- odag lambda.
+// odag, dmat: 16 complex (float2 for C64, double2 for C128) on the device.
+cudaError_t launch_adjoint_gate(int precision, void* psi, void* lam, int L, int bond,
+                                const void* odag, const void* dmat, double* partial,
+                                const LaunchCfg& cfg, cudaStream_t s);
+
+// out[0] = sum of partials[0..n) (times 2 when times_two), fixed order.
+cudaError_t launch_grad_reduce(const double* partials, long long n, double* out, int times_two,
+                               cudaStream_t s);
+
 }  // namespace fsv

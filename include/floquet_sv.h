@@ -275,6 +275,52 @@ int sv_host_period_gates(int L, const sv_floquet_params *p, int *n_gates,
 int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
                         int *window_lo, int *gate_count, double *unitaries_out);
 
+/* ------------------------------------------------------------------ batch
+ * Many independent chains (each its own L, parameters and product state)
+ * evolved together on one device.  Chains of up to 14 sites can stay in one
+ * CTA's shared memory for a whole run (resident form); the others run the
+ * plain or block forms.  One CUDA graph advances every chain by a run of
+ * periods, the chains as independent branches.  An autotuner times the
+ * forms that fit each distinct L on a few of its chains and keeps the
+ * fastest (chain-periods per second).
+ */
+typedef struct sv_batch sv_batch;
+
+#define SV_BATCH_AUTO (-1)      /* autotune per distinct L */
+#define SV_BATCH_PLAIN 0        /* per-gate passes */
+#define SV_BATCH_BLOCK_SIMT 1   /* fused n = 6 windows on CUDA cores */
+#define SV_BATCH_BLOCK_TC 2     /* fused n = 6 windows on the tensor cores (L >= 13) */
+#define SV_BATCH_RESIDENT 3     /* state in one CTA's shared memory (L <= 14) */
+
+/* Bytes of the state buffer for n_chains chains of sizes L[0..n_chains):
+ * complex64 states back to back, each starting on a 256-byte boundary. */
+size_t sv_batch_state_bytes(int n_chains, const int *L);
+
+/*
+ * Create a batch on `device` and initialise every chain's product state.
+ * L: n_chains sizes (2..34); params: n_chains parameter sets (mode, split,
+ * block_n and per-period arrays are ignored / must be absent); product_states:
+ * the chains' spinors back to back (4 L_c doubles each, as sv_init);
+ * state_dev: caller-owned device buffer of >= sv_batch_state_bytes bytes;
+ * form: SV_BATCH_AUTO or one SV_BATCH_* form for every chain (a form a
+ * chain cannot use falls back to SV_BATCH_PLAIN).  Errors: SV_EINVAL,
+ * SV_ENOMEM, SV_ECUDA (*out is NULL on error).
+ */
+int sv_batch_create(sv_batch **out, int device, int n_chains, const int *L,
+                    const sv_floquet_params *params, const double *product_states,
+                    void *state_dev, size_t bytes, int form, void *cuda_stream);
+
+/* Advance every chain by `periods`; energy_out / norm_out (nullable, host):
+ * [n_chains][periods] row-major energy densities (normalised state) and
+ * norms.  Errors: SV_EINVAL, SV_ECUDA, SV_ETIMEOUT. */
+int sv_batch_evolve(sv_batch *b, int64_t periods, double *energy_out, double *norm_out);
+
+/* The SV_BATCH_* form each chain runs (host array of n_chains). */
+int sv_batch_forms(const sv_batch *b, int *form_out);
+
+const char *sv_batch_last_error(const sv_batch *b);
+void sv_batch_destroy(sv_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

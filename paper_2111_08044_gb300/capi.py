@@ -27,6 +27,11 @@ SV_MODE_PLAIN = 0
 SV_MODE_BLOCK = 1
 SV_SPLIT_BF16X3 = 0
 SV_SPLIT_FP32 = 1
+SV_BATCH_AUTO = -1
+SV_BATCH_PLAIN = 0
+SV_BATCH_BLOCK_SIMT = 1
+SV_BATCH_BLOCK_TC = 2
+SV_BATCH_RESIDENT = 3
 
 _ERRNAMES = {SV_EINVAL: "SV_EINVAL", SV_ENOMEM: "SV_ENOMEM", SV_ECUDA: "SV_ECUDA",
              SV_ETIMEOUT: "SV_ETIMEOUT", SV_ESTATE: "SV_ESTATE",
@@ -90,6 +95,13 @@ SIGNATURES = {
     "sv_host_bond_gates": ([_i32, _pp, _dp, _dp], _i32),
     "sv_host_period_gates": ([_i32, _pp, _ip, _ip, _dp], _i32),
     "sv_host_fusion_plan": ([_i32, _pp, _i32, _ip, _ip, _ip, _dp], _i32),
+    "sv_batch_state_bytes": ([_i32, _ip], _sz),
+    "sv_batch_create": ([ctypes.POINTER(_vp), _i32, _i32, _ip, _pp, _dp, _vp, _sz, _i32, _vp],
+                        _i32),
+    "sv_batch_evolve": ([_vp, _i64, _dp, _dp], _i32),
+    "sv_batch_forms": ([_vp, _ip], _i32),
+    "sv_batch_last_error": ([_vp], ctypes.c_char_p),
+    "sv_batch_destroy": ([_vp], None),
 }
 
 _lib = None

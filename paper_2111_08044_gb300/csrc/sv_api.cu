@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "sv_batch.h"
 #include "sv_block.h"
 #include "sv_internal.h"
 #include "sv_kernels.h"
@@ -205,6 +206,99 @@ int ensure_graph(sv_ctx* ctx) {
   return SV_OK;
 }
 
+int read_ring(sv_ctx* ctx, int64_t c0, int64_t count, double* e_out, double* n_out);
+
+}  // namespace
+
+// Hooks for the batch executor (sv_batch.cu); not part of the C ABI.
+namespace fsv {
+
+int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out) {
+  *out = nullptr;
+  if (!ctx || !ctx->built) return SV_ESTATE;
+  DeviceGuard dg(ctx->device);
+  SV_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed),
+          "begin capture");
+  int rc = enqueue_period(ctx, ctx->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  if (rc != SV_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  *out = g;
+  return SV_OK;
+}
+
+void ctx_advance(sv_ctx* ctx, int64_t periods) { ctx->counter += periods; }
+
+int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n) {
+  return read_ring(ctx, c0, count, e, n);
+}
+
+int ctx_ring_len() { return kRing; }
+
+namespace {
+double unitarity_defect(const double* re, const double* im) {
+  double d = 0.0, tr = 0.0;
+  for (int k = 0; k < 4; ++k)
+    for (int l = 0; l < 4; ++l) {
+      double sr = 0.0, si = 0.0;  // (M^dagger M)_{kl} = sum_i conj(M_ik) M_il
+      for (int i = 0; i < 4; ++i) {
+        sr += re[4 * i + k] * re[4 * i + l] + im[4 * i + k] * im[4 * i + l];
+        si += re[4 * i + k] * im[4 * i + l] - im[4 * i + k] * re[4 * i + l];
+      }
+      if (k == l) {
+        sr -= 1.0;
+        tr += sr;
+      }
+      d += sr * sr + si * si;
+    }
+  return d + tr * tr;
+}
+}  // namespace
+
+void round_unitary4(const cd* m, float2* out) {
+  float f[32];
+  double re[16], im[16];
+  for (int k = 0; k < 16; ++k) {
+    f[2 * k] = (float)m[k].real();
+    f[2 * k + 1] = (float)m[k].imag();
+  }
+  auto load = [&]() {
+    for (int k = 0; k < 16; ++k) {
+      re[k] = f[2 * k];
+      im[k] = f[2 * k + 1];
+    }
+  };
+  load();
+  double best = unitarity_defect(re, im);
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    bool moved = false;
+    for (int e = 0; e < 32; ++e) {
+      const float orig = f[e];
+      for (int dir = -1; dir <= 1; dir += 2) {
+        f[e] = std::nextafter(orig, dir > 0 ? INFINITY : -INFINITY);
+        load();
+        const double d = unitarity_defect(re, im);
+        if (d < best) {
+          best = d;
+          moved = true;
+          break;
+        }
+        f[e] = orig;
+      }
+    }
+    if (!moved) break;
+  }
+  for (int k = 0; k < 16; ++k) out[k] = make_float2(f[2 * k], f[2 * k + 1]);
+}
+
+}  // namespace fsv
+
+namespace {
+
 int check_ready(sv_ctx* ctx, bool need_built) {
   if (!ctx) return SV_EINVAL;
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
@@ -304,66 +398,14 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
 
 // Defect of D = M^dagger M - I (4x4, FP64): |D|_F^2 + tr(D)^2.  The trace
 // term is the mean norm change per application on a maximally mixed pair.
-double unitarity_defect(const double* re, const double* im) {
-  double d = 0.0, tr = 0.0;
-  for (int k = 0; k < 4; ++k)
-    for (int l = 0; l < 4; ++l) {
-      double sr = 0.0, si = 0.0;  // (M^dagger M)_{kl} = sum_i conj(M_ik) M_il
-      for (int i = 0; i < 4; ++i) {
-        sr += re[4 * i + k] * re[4 * i + l] + im[4 * i + k] * im[4 * i + l];
-        si += re[4 * i + k] * im[4 * i + l] - im[4 * i + k] * re[4 * i + l];
-      }
-      if (k == l) {
-        sr -= 1.0;
-        tr += sr;
-      }
-      d += sr * sr + si * si;
-    }
-  return d + tr * tr;
-}
 
 // FP32 copy of a 4x4 unitary: nearest rounding, then a coordinate descent
 // over one-ulp moves of each entry that lowers the distance of the FP32
 // matrix from unitarity (a plain rounding leaves a defect whose sign repeats
 // every time the gate is applied, so the norm would drift steadily).
-void round_unitary4(const cd* m, float2* out) {
-  float f[32];
-  double re[16], im[16];
-  for (int k = 0; k < 16; ++k) {
-    f[2 * k] = (float)m[k].real();
-    f[2 * k + 1] = (float)m[k].imag();
-  }
-  auto load = [&]() {
-    for (int k = 0; k < 16; ++k) {
-      re[k] = f[2 * k];
-      im[k] = f[2 * k + 1];
-    }
-  };
-  load();
-  double best = unitarity_defect(re, im);
-  for (int sweep = 0; sweep < 20; ++sweep) {
-    bool moved = false;
-    for (int e = 0; e < 32; ++e) {
-      const float orig = f[e];
-      for (int dir = -1; dir <= 1; dir += 2) {
-        f[e] = std::nextafter(orig, dir > 0 ? INFINITY : -INFINITY);
-        load();
-        const double d = unitarity_defect(re, im);
-        if (d < best) {
-          best = d;
-          moved = true;
-          break;
-        }
-        f[e] = orig;
-      }
-    }
-    if (!moved) break;
-  }
-  for (int k = 0; k < 16; ++k) out[k] = make_float2(f[2 * k], f[2 * k + 1]);
-}
 
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<float2>& out, size_t at) {
-  for (size_t g = 0; g < gates.size(); ++g) round_unitary4(gates[g].m, &out[at + 16 * g]);
+  for (size_t g = 0; g < gates.size(); ++g) fsv::round_unitary4(gates[g].m, &out[at + 16 * g]);
 }
 
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<double2>& out, size_t at) {
@@ -709,7 +751,7 @@ int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_
           tab64[at + 16 + e] = make_double2(op.d[e].real(), op.d[e].imag());
         }
       } else {
-        round_unitary4(op.odag, &tab32[at]);
+        fsv::round_unitary4(op.odag, &tab32[at]);
         for (int e = 0; e < 16; ++e)
           tab32[at + 16 + e] = make_float2((float)op.d[e].real(), (float)op.d[e].imag());
       }

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/floquet_sv.h"
 
 namespace fsv {
@@ -17,6 +19,23 @@ using cd = std::complex<double>;
 // its gate is applied (the gate is the last one of the period on that site,
 // or the last gate of the period).
 enum : int { EPI_X_HI = 1, EPI_X_LO = 2, EPI_DIAG = 4 };
+
+}  // namespace fsv
+
+struct sv_ctx;
+
+namespace fsv {
+
+// Batch-executor hooks into a context (sv_api.cu).
+// One period of the built evolution captured as a graph template (the
+// caller destroys it); the graph advances the device period counter.
+int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out);
+// Account for periods run through such graphs on the host mirror.
+void ctx_advance(sv_ctx* ctx, int64_t periods);
+// (energy density, norm) of periods c0 .. c0+count-1 from the energy ring.
+int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n);
+// Periods the energy ring holds.
+int ctx_ring_len();
 
 struct Gate2 {
   int bond = 0;      // acts on sites (bond, bond + 1)

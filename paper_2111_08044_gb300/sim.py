@@ -172,3 +172,92 @@ def chain_params(cfg, **over):
         kw["hx_p"] = cfg.hx_p
     kw.update(over)
     return kw
+
+
+class FloquetBatch:
+    """Many independent chains (uneven L, per-chain parameters) evolved
+    together on one GPU through the batch calls of the C ABI.
+
+    >>> b = FloquetBatch(inputs.batch_preset(512))
+    >>> e, n = b.evolve(100)          # [n_chains, periods] each
+    >>> b.forms()                     # SV_BATCH_* form per chain
+    """
+
+    def __init__(self, chains, form: int = capi.SV_BATCH_AUTO, device: int = 0, stream=None):
+        import torch
+        self._torch = torch
+        self.n = len(chains)
+        self.L = np.array([c.L for c in chains], dtype=np.int32)
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._lib = capi.load()
+        total = int(self._lib.sv_batch_state_bytes(self.n, self.L.ctypes.data_as(capi._ip)))
+        if total == 0:
+            raise ValueError("chain sizes must be in 2..34")
+        self.state = torch.empty(total, dtype=torch.uint8, device=self.device)
+        params = (capi.sv_floquet_params * self.n)()
+        for k, c in enumerate(chains):
+            p, _ = capi.make_params(J=c.J, hx=c.hx, hz=c.hz, T=c.T, theta=c.theta,
+                                    edge_field_weight=c.edge_field_weight, K=c.K,
+                                    first_layer=c.first_layer)
+            params[k] = p
+        self._params = params
+        sp = np.ascontiguousarray(np.concatenate([c.spinors().reshape(-1) for c in chains]),
+                                  dtype=np.float64)
+        b = ctypes.c_void_p()
+        rc = self._lib.sv_batch_create(ctypes.byref(b), self.device.index or 0, self.n,
+                                       self.L.ctypes.data_as(capi._ip), params,
+                                       sp.ctypes.data_as(capi._dp),
+                                       ctypes.c_void_p(self.state.data_ptr()), total, int(form),
+                                       ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != capi.SV_OK:
+            raise capi.SvError(rc, "sv_batch_create")
+        self._b = b
+        self.offsets = []
+        off = 0
+        for L in self.L:
+            off = (off + 255) // 256 * 256
+            self.offsets.append(off)
+            off += 8 << int(L)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.sv_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != capi.SV_OK:
+            m = self._lib.sv_batch_last_error(self._b)
+            raise capi.SvError(rc, f"{what}: {m.decode() if m else ''}")
+
+    def evolve(self, periods: int):
+        e = np.zeros((self.n, max(periods, 1)))
+        nn = np.zeros((self.n, max(periods, 1)))
+        self._check(self._lib.sv_batch_evolve(self._b, int(periods), e.ctypes.data_as(capi._dp),
+                                              nn.ctypes.data_as(capi._dp)), "sv_batch_evolve")
+        return e[:, :periods], nn[:, :periods]
+
+    def forms(self) -> np.ndarray:
+        out = np.zeros(self.n, dtype=np.int32)
+        self._check(self._lib.sv_batch_forms(self._b, out.ctypes.data_as(capi._ip)),
+                    "sv_batch_forms")
+        return out
+
+    def chain_state(self, c: int) -> np.ndarray:
+        """Host copy of chain c's complex64 state."""
+        self._torch.cuda.synchronize(self.device)
+        L = int(self.L[c])
+        raw = self.state[self.offsets[c]:self.offsets[c] + (8 << L)]
+        return raw.view(self._torch.complex64).cpu().numpy()

@@ -146,3 +146,18 @@ def test_fusion_plan_shape_large_chains(svlib, L, n):
     jumps = np.abs(np.diff(np.concatenate([lo, [0]])))
     assert jumps.max() <= 7  # every relabel fits in a 7-bit row index
     assert len(lo) <= {6: 21, 7: 18}[n]
+
+
+def test_batch_host_checks(svlib):
+    import ctypes
+    L = np.array([14, 22, 2], dtype=np.int32)
+    total = svlib.sv_batch_state_bytes(3, L.ctypes.data_as(capi._ip))
+    # 256-byte aligned chain slices of 8 * 2^L bytes
+    assert total == (8 << 14) + (8 << 22) + (8 << 2)
+    bad = np.array([14, 35], dtype=np.int32)
+    assert svlib.sv_batch_state_bytes(2, bad.ctypes.data_as(capi._ip)) == 0
+    b = ctypes.c_void_p()
+    p = (capi.sv_floquet_params * 1)()
+    assert svlib.sv_batch_create(ctypes.byref(b), 0, 0, None, p, None, None, 0, -1,
+                                 None) == capi.SV_EINVAL
+    assert not b.value

@@ -44,6 +44,8 @@ def _parse():
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-periods", type=int, default=64,
+                    help="periods of the 512-chain batch line (0 skips it)")
     return ap.parse_args()
 
 
@@ -210,6 +212,49 @@ def _e2e(args, steps, rank, local):
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16}
 
 
+def _batch(args, local):
+    """The 512-chain batch (L 14..22, per-chain couplings): chain-periods/s
+    over args.batch_periods periods after a warm-up run of 16, with the
+    build and autotuning timed separately."""
+    import numpy as np
+    import torch
+
+    from paper_2111_08044_gb300 import inputs
+    from paper_2111_08044_gb300.sim import FloquetBatch
+
+    chains = inputs.batch_preset(512)
+    t0 = time.perf_counter()
+    b = FloquetBatch(chains, device=local)
+    t_create = time.perf_counter() - t0
+    b.evolve(16)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(b.stream)
+    e, n = b.evolve(args.batch_periods)
+    end.record(b.stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    forms = b.forms()
+    Ls = np.array([c.L for c in chains])
+    amps = float(sum(1 << int(L) for L in Ls))
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+    names = {0: "plain", 1: "block_simt", 2: "block_tc", 3: "resident"}
+    return {
+        "workload": "512 chains, L uniform 14..22, J~U[0.8,1.2] hx~U[0.6,1.0] hz~U[0.2,0.6] "
+                    "theta~U[0.1,0.5], random product states (seed 2), complex64",
+        "chain_periods_per_s": 512 * args.batch_periods / (ms / 1e3),
+        "periods": args.batch_periods,
+        "ms": ms,
+        "create_and_autotune_s": t_create,
+        "amplitudes": amps,
+        "forms": {names[k]: int((forms == k).sum()) for k in range(4) if (forms == k).any()},
+        "norm_max_dev": float(np.abs(n - 1.0).max()),
+    }
+
+
 def _oracle_periods_per_s(L_sample: int, periods: int, seed: int):
     """FP64 oracle on the host cores: `periods` full periods at L_sample,
     scaled to L=30 by amplitudes x two-qubit gates per period."""
@@ -293,6 +338,7 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = _e2e(args, args.steps, rank, local)
         e2e["value"] = world * e2e["value"]  # replicas run side by side
+    batch = _batch(args, local) if args.batch_periods > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt = _oracle_periods_per_s(24, 2, seed=4)
@@ -327,6 +373,7 @@ def run_ours(args):
         "two_qubit_gates_per_s": value * block["gates_per_period"] / world * world,
         "gpu_launches": gpl,
         "clocks": ck,
+        "batch": batch,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }

@@ -1,0 +1,86 @@
+"""Error accumulation of the complex64 forms over many periods.
+
+The complex64 plain and tensor-core block forms run in lockstep with the
+complex128 check mode; that reference is the same circuit in FP64 and
+agrees with the FP64 CPU oracle to 1e-11 wherever the oracle can run.
+
+Every `every` periods the study records, for each complex64 form:
+- the largest energy-density error over the chunk;
+- the state infidelity 1 - |<psi_ref|psi>|^2 / (|psi_ref|^2 |psi|^2);
+- the norm drift.
+
+The infidelity is computed on the device in FP64. This mirrors the paper's
+accuracy study of long f32 runs against a reference (Sec. V).
+
+    python -m paper_2111_08044_gb300.accuracy --L 26 --periods 1000 --every 100
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+from . import capi, inputs
+from .sim import FloquetSimulator, chain_params
+
+FORMS = {
+    "plain": dict(mode=capi.SV_MODE_PLAIN),
+    "block_tc": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_BF16X3),
+    "block_simt": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_FP32),
+}
+
+
+def _infidelity(ref, psi):
+    import torch
+    a = ref.state
+    b = psi.state.to(torch.complex128)
+    ov = torch.vdot(a, b)
+    na = torch.vdot(a, a).real
+    nb = torch.vdot(b, b).real
+    return float(1.0 - (ov.abs() ** 2) / (na * nb))
+
+
+def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
+    cfg = inputs.ChainConfig(L=L, seed=seed)
+    ref = FloquetSimulator(L, precision="c128")
+    ref.init_product_state(cfg.spinors())
+    ref.build(**chain_params(cfg))
+    sims = {}
+    for name in forms:
+        s = FloquetSimulator(L)
+        s.init_product_state(cfg.spinors())
+        s.build(**chain_params(cfg, **FORMS[name]))
+        sims[name] = s
+    rows = []
+    done = 0
+    while done < periods:
+        k = min(every, periods - done)
+        e_ref, n_ref = ref.evolve(k)
+        done += k
+        row = {"period": done, "energy_ref": float(e_ref[-1]), "norm_ref_dev": float(n_ref[-1] - 1)}
+        for name, s in sims.items():
+            e, n = s.evolve(k)
+            row[name] = {"max_abs_energy_err": float(np.max(np.abs(e - e_ref))),
+                         "infidelity": _infidelity(ref, s),
+                         "norm_dev": float(n[-1] - 1.0)}
+        rows.append(row)
+    for s in list(sims.values()) + [ref]:
+        s.close()
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=26)
+    ap.add_argument("--periods", type=int, default=1000)
+    ap.add_argument("--every", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--forms", default="plain,block_tc")
+    a = ap.parse_args()
+    for row in study(a.L, a.periods, a.every, a.seed, tuple(a.forms.split(","))):
+        print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()

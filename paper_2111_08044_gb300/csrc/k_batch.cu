@@ -35,9 +35,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   for (int p = 0; p < periods; ++p) {
     for (int g = 0; g < ch.ngates; ++g) {
       const int b = ch.bonds[g];
-      float2 G[16];
+      float2 G[16], Gl[16];  // gate and its FP32 rounding residual
 #pragma unroll
-      for (int k = 0; k < 16; ++k) G[k] = ch.gates[16 * g + k];
+      for (int k = 0; k < 16; ++k) {
+        G[k] = ch.gates[kGateEntries * g + k];
+        Gl[k] = ch.gates[kGateEntries * g + 16 + k];
+      }
       const uint32_t lowmask = (1u << b) - 1;
       // local index r = 2 b_b + b_{b+1}: offsets of r = 0..3
       const uint32_t o1 = 2u << b, o2 = 1u << b, o3 = 3u << b;
@@ -47,12 +50,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2 w[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          float2 a = czero<float2>();
+          float2 a = czero<float2>(), lo = czero<float2>();
           a = cmac(a, G[4 * r + 0], v0);
           a = cmac(a, G[4 * r + 1], v1);
           a = cmac(a, G[4 * r + 2], v2);
           a = cmac(a, G[4 * r + 3], v3);
-          w[r] = a;
+          lo = cmac(lo, Gl[4 * r + 0], v0);
+          lo = cmac(lo, Gl[4 * r + 1], v1);
+          lo = cmac(lo, Gl[4 * r + 2], v2);
+          lo = cmac(lo, Gl[4 * r + 3], v3);
+          w[r] = make_float2(a.x + lo.x, a.y + lo.y);
         }
         sp[x] = w[0];
         sp[x + o1] = w[1];

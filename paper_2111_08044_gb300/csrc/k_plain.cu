@@ -50,12 +50,17 @@ __global__ void __launch_bounds__(kThreads) k_gate_high(
   constexpr int NV = CT<R>::NV, LV = CT<R>::LV;
   const C* gp = gate_ptr(gate_base, stride, counter);
   const R sc = (R)renorm_scale(ep.rn);
-  C g[16];
+  // the gate as hi + lo parts (lo = 0 in FP64): the FP32 table's rounding
+  // error is carried along instead of being applied every period
+  C g[16], gl[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     g[k] = gp[k];
     g[k].x *= sc;
     g[k].y *= sc;
+    gl[k] = gp[16 + k];
+    gl[k].x *= sc;
+    gl[k].y *= sc;
   }
   Diag<R> dg;
   if (ep.flags & EPI_DIAG) dg.init(ep, L);
@@ -92,9 +97,14 @@ __global__ void __launch_bounds__(kThreads) k_gate_high(
       for (int k = 0; k < NV; ++k)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          C acc = czero<C>();
+          C acc = czero<C>(), lo = czero<C>();
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc = cmac(acc, g[4 * r + c], v[c][k]);
+          for (int c = 0; c < 4; ++c) {
+            acc = cmac(acc, g[4 * r + c], v[c][k]);
+            if (kGateLo<R>) lo = cmac(lo, gl[4 * r + c], v[c][k]);
+          }
+          acc.x += lo.x;
+          acc.y += lo.y;
           w[r][k] = acc;
         }
       if (store) {
@@ -182,9 +192,9 @@ __global__ void __launch_bounds__(kThreads) k_gate_low(
   using C = typename CT<R>::C;
   using V = typename CT<R>::V;
   constexpr int NV = CT<R>::NV, LV = CT<R>::LV;
-  __shared__ C gs[16];
+  __shared__ C gs[kGateEntries];  // hi parts, then lo parts
   const C* gp = gate_ptr(gate_base, stride, counter);
-  if (threadIdx.x < 16) {
+  if (threadIdx.x < kGateEntries) {
     const R sc = (R)renorm_scale(ep.rn);
     C g = gp[threadIdx.x];
     g.x *= sc;
@@ -225,6 +235,15 @@ __global__ void __launch_bounds__(kThreads) k_gate_low(
         acc = cmac(acc, gs[4 * r + (r ^ 1)], p1[c][k]);
         acc = cmac(acc, gs[4 * r + (r ^ 2)], p2[c][k]);
         acc = cmac(acc, gs[4 * r + (r ^ 3)], p3[c][k]);
+        if (kGateLo<R>) {
+          C lo = czero<C>();
+          lo = cmac(lo, gs[16 + 4 * r + r], a[c][k]);
+          lo = cmac(lo, gs[16 + 4 * r + (r ^ 1)], p1[c][k]);
+          lo = cmac(lo, gs[16 + 4 * r + (r ^ 2)], p2[c][k]);
+          lo = cmac(lo, gs[16 + 4 * r + (r ^ 3)], p3[c][k]);
+          acc.x += lo.x;
+          acc.y += lo.y;
+        }
         w[c][k] = acc;
       }
     if (store) {
@@ -296,9 +315,14 @@ __global__ void __launch_bounds__(kThreads) k_gate_small(
     for (int r = 0; r < 4; ++r) v[r] = psi[x + off[r]];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      C acc = czero<C>();
+      C acc = czero<C>(), lo = czero<C>();
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = cmac(acc, gp[4 * r + c], v[c]);
+      for (int c = 0; c < 4; ++c) {
+        acc = cmac(acc, gp[4 * r + c], v[c]);
+        if (kGateLo<R>) lo = cmac(lo, gp[16 + 4 * r + c], v[c]);
+      }
+      acc.x += lo.x;
+      acc.y += lo.y;
       acc.x *= sc;
       acc.y *= sc;
       w[r] = acc;

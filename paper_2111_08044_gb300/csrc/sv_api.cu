@@ -155,7 +155,7 @@ fsv::Renorm renorm_of(const sv_ctx* ctx) {
 int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
   const int ng = (int)ctx->gates.size();
   const size_t cbytes = amp_bytes(ctx->precision);
-  const long long stride = ctx->n_period_params > 0 ? (long long)ng * 16 : 0;
+  const long long stride = ctx->n_period_params > 0 ? (long long)ng * fsv::kGateEntries : 0;
   int slot = 0;
   for (int g = 0; g < ng; ++g) {
     const fsv::Gate2& gt = ctx->gates[g];
@@ -163,7 +163,7 @@ int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
     if (gt.epi) ++slot;
     fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
     if (g == 0) ep.rn = renorm_of(ctx);
-    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
+    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * fsv::kGateEntries * cbytes;
     SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
                                    ctx->d_counter, ep, 1, ctx->cfg, s),
             "plain gate launch");
@@ -373,7 +373,7 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
   }
   const int ng = (int)ctx->gates.size();
   const size_t cbytes = amp_bytes(ctx->precision);
-  const long long stride = ctx->n_period_params > 0 ? (long long)ng * 16 : 0;
+  const long long stride = ctx->n_period_params > 0 ? (long long)ng * fsv::kGateEntries : 0;
   int slot = 0;
   for (int g = 0; g < ng; ++g) {
     const fsv::Gate2& gt = ctx->gates[g];
@@ -381,7 +381,7 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
     if (gt.epi) ++slot;
     fsv::EpiParams ep = epi_for(ctx, gt.epi, gt.bond, part);
     if (g == 0) ep.rn = renorm_of(ctx);
-    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * 16 * cbytes;
+    const char* gb = static_cast<const char*>(ctx->d_gates) + (size_t)g * fsv::kGateEntries * cbytes;
     SV_CUDA(cudaEventRecord(ev[g], s), "event record");
     SV_CUDA(fsv::launch_plain_gate(ctx->precision, ctx->state, ctx->L, gt.bond, gb, stride,
                                    ctx->d_counter, ep, 1, ctx->cfg, s),
@@ -405,13 +405,22 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
 // every time the gate is applied, so the norm would drift steadily).
 
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<float2>& out, size_t at) {
-  for (size_t g = 0; g < gates.size(); ++g) fsv::round_unitary4(gates[g].m, &out[at + 16 * g]);
+  for (size_t g = 0; g < gates.size(); ++g) {
+    float2* e = &out[at + fsv::kGateEntries * g];
+    fsv::round_unitary4(gates[g].m, e);
+    for (int k = 0; k < 16; ++k)
+      e[16 + k] = make_float2((float)(gates[g].m[k].real() - (double)e[k].x),
+                              (float)(gates[g].m[k].imag() - (double)e[k].y));
+  }
 }
 
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<double2>& out, size_t at) {
   for (size_t g = 0; g < gates.size(); ++g)
-    for (int k = 0; k < 16; ++k)
-      out[at + 16 * g + k] = make_double2(gates[g].m[k].real(), gates[g].m[k].imag());
+    for (int k = 0; k < 16; ++k) {
+      out[at + fsv::kGateEntries * g + k] =
+          make_double2(gates[g].m[k].real(), gates[g].m[k].imag());
+      out[at + fsv::kGateEntries * g + 16 + k] = make_double2(0.0, 0.0);
+    }
 }
 
 }  // namespace
@@ -452,16 +461,16 @@ int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
   ok = ok && cudaMalloc(&ctx->d_ring, sizeof(double) * 2 * kRing) == cudaSuccess;
   ok = ok && cudaMalloc(&ctx->d_meas, sizeof(double) * 2) == cudaSuccess;
   ok = ok && cudaMalloc(&ctx->d_counter, sizeof(long long)) == cudaSuccess;
-  ok = ok && cudaMalloc(&ctx->d_ident, 16 * 16) == cudaSuccess;
+  ok = ok && cudaMalloc(&ctx->d_ident, 16 * fsv::kGateEntries) == cudaSuccess;
   ok = ok && cudaMalloc(&ctx->d_part_meas, sizeof(double) * 2 * ctx->maxb *
                                                ctx->part_slots_meas) == cudaSuccess;
   if (ok) {
     if (precision == SV_C128) {
-      double2 id[16] = {};
+      double2 id[fsv::kGateEntries] = {};  // identity, zero residual
       for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0;
       ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
     } else {
-      float2 id[16] = {};
+      float2 id[fsv::kGateEntries] = {};
       for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0f;
       ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
     }
@@ -573,7 +582,7 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
   } else {
     const int64_t ntab = p->n_period_params > 0 ? p->n_period_params : 1;
     const size_t cb = amp_bytes(ctx->precision);
-    ctx->d_gates_bytes = (size_t)ntab * ng * 16 * cb;
+    ctx->d_gates_bytes = (size_t)ntab * ng * fsv::kGateEntries * cb;
     if (cudaMalloc(&ctx->d_gates, ctx->d_gates_bytes) != cudaSuccess) {
       cudaGetLastError();
       ctx->d_gates = nullptr;
@@ -590,22 +599,22 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
     }
     SV_CUDA(cudaMemsetAsync(ctx->d_part_evolve, 0, pbytes, ctx->stream), "memset partials");
     if (ctx->precision == SV_C128) {
-      std::vector<double2> tab((size_t)ntab * ng * 16);
+      std::vector<double2> tab((size_t)ntab * ng * fsv::kGateEntries);
       for (int64_t k = 0; k < ntab; ++k) {
         auto gk = k == 0 ? ctx->gates
                          : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
-        upload_gates(gk, tab, (size_t)k * ng * 16);
+        upload_gates(gk, tab, (size_t)k * ng * fsv::kGateEntries);
       }
       SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
                               cudaMemcpyHostToDevice, ctx->stream),
               "upload gates");
       SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
     } else {
-      std::vector<float2> tab((size_t)ntab * ng * 16);
+      std::vector<float2> tab((size_t)ntab * ng * fsv::kGateEntries);
       for (int64_t k = 0; k < ntab; ++k) {
         auto gk = k == 0 ? ctx->gates
                          : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
-        upload_gates(gk, tab, (size_t)k * ng * 16);
+        upload_gates(gk, tab, (size_t)k * ng * fsv::kGateEntries);
       }
       SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
                               cudaMemcpyHostToDevice, ctx->stream),

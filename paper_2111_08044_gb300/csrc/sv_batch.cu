@@ -120,9 +120,12 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
     auto pg = fsv::period_gates(b->L[c], p, p.theta, p.hx);
     goff[k] = bonds.size();
     for (auto& g : pg) {
-      float2 m[16];
+      float2 m[fsv::kGateEntries];
       fsv::round_unitary4(g.m, m);
-      gates.insert(gates.end(), m, m + 16);
+      for (int e = 0; e < 16; ++e)
+        m[16 + e] = make_float2((float)(g.m[e].real() - (double)m[e].x),
+                                (float)(g.m[e].imag() - (double)m[e].y));
+      gates.insert(gates.end(), m, m + fsv::kGateEntries);
       bonds.push_back(g.bond);
     }
     fsv::Observable o = fsv::observable(b->L[c], p);
@@ -149,7 +152,7 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
   for (size_t k = 0; k < chains.size(); ++k) {
     fsv::ResidentChain& r = hd[k];
     r.psi = reinterpret_cast<float2*>(b->base + b->off[chains[k]]);
-    r.gates = rs->d_gates + 16 * goff[k];
+    r.gates = rs->d_gates + fsv::kGateEntries * goff[k];
     r.bonds = rs->d_bonds + goff[k];
     r.ring = rs->d_ring + 2 * (size_t)ring * k;
   }

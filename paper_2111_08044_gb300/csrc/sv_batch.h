@@ -6,6 +6,7 @@
 #include <cstddef>
 
 #include "sv_internal.h"
+#include "sv_kernels.h"
 
 namespace fsv {
 

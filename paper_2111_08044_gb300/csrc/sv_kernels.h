@@ -31,6 +31,14 @@ struct EpiParams {
   Renorm rn;                  // set on the first pass of a period only
 };
 
+// A gate table entry: 16 complex of the gate (row-major, local index
+// r = 2 b_bond + b_{bond+1}) followed by 16 complex of its rounding
+// residual (zero for FP64 tables), so that FP32 passes apply the FP64 gate
+// to within 2^-48 instead of its FP32 rounding.
+constexpr int kGateEntries = 32;
+template <typename R>
+constexpr bool kGateLo = sizeof(R) == 4;
+
 struct LaunchCfg {
   int num_sms = 148;
 };

@@ -25,11 +25,12 @@ constexpr int kMaxBlocks = 1024;
 constexpr size_t kScratchDoubles = (size_t)2 * kMaxPasses * kMaxBlocks;  // 288 KiB
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
-static __device__ __align__(256) float2 g_ident64[16] = {
+// identity gates with zero residual parts (kGateEntries complex each)
+static __device__ __align__(256) float2 g_ident64[fsv::kGateEntries] = {
     {1.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f},
     {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}, {0.f, 0.f},
     {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {1.f, 0.f}};
-static __device__ __align__(256) double2 g_ident128[16] = {
+static __device__ __align__(256) double2 g_ident128[fsv::kGateEntries] = {
     {1.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {1.0, 0.0},
     {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {1.0, 0.0}, {0.0, 0.0},
     {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {1.0, 0.0}};

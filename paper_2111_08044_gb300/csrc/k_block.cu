@@ -177,7 +177,9 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   bp->tensor_cores = split == SV_SPLIT_BF16X3 && block_tc_supported(L, n);
   const long long ntiles = 1ll << (L - n - R);
   const int per_sm = bp->tensor_cores ? 1 : 2;
-  bp->grid = (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)cfg.num_sms * per_sm));
+  long long grid = std::min<long long>(ntiles, (long long)cfg.num_sms * per_sm);
+  if (cfg.min_tiles_per_cta > 0) grid = std::min<long long>(grid, ntiles / cfg.min_tiles_per_cta);
+  bp->grid = (int)std::max<long long>(1, grid);
   bp->maxb = bp->grid;
   auto fail = [&](const std::string& m) {
     *msg = m;

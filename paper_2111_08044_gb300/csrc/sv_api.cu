@@ -233,6 +233,8 @@ int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out) {
 
 void ctx_advance(sv_ctx* ctx, int64_t periods) { ctx->counter += periods; }
 
+void ctx_set_min_tiles(sv_ctx* ctx, int tiles) { ctx->cfg.min_tiles_per_cta = tiles; }
+
 int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n) {
   return read_ring(ctx, c0, count, e, n);
 }

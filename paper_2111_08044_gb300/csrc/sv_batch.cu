@@ -12,8 +12,9 @@
 //
 // The autotuner (form SV_BATCH_AUTO) times every form that fits a distinct
 // L on up to eight of its chains, run together for four periods through the
-// same kind of graph, and keeps the form with the most chain-periods per
-// second for all chains of that L.
+// same kind of graph (block forms with 4, 8 or 16 tiles per CTA at least),
+// and keeps the fastest (most chain-periods per second) for all chains of
+// that L.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +37,7 @@ struct sv_batch {
   std::vector<int> L;
   std::vector<size_t> off;
   std::vector<int> form;
+  std::vector<int> min_tiles;  // block forms: tiles per CTA at least
   std::vector<sv_floquet_params> params;
   std::vector<const double*> spinors;  // caller's arrays, valid during create only
   std::vector<sv_ctx*> ctx;
@@ -57,6 +59,11 @@ struct sv_batch {
 namespace {
 
 constexpr size_t kAlign = 256;
+// Block passes of a batch share the device with other chains' passes: each
+// CTA keeps a run of tiles long enough to fill its pipeline.  The
+// autotuner picks the run length per L among these.
+constexpr int kTileRuns[3] = {4, 8, 16};
+constexpr int kDefaultTileRun = 8;
 
 int bfail(sv_batch* b, int code, const char* fmt, ...) {
   if (b) {
@@ -172,7 +179,8 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
 }
 
 // Build the period evolution of chain c in its context for a graph form.
-int build_graph_form(sv_batch* b, int c, int form) {
+int build_graph_form(sv_batch* b, int c, int form, int min_tiles) {
+  fsv::ctx_set_min_tiles(b->ctx[c], min_tiles);
   sv_floquet_params p = b->params[c];
   p.theta_p = nullptr;
   p.hx_p = nullptr;
@@ -252,7 +260,8 @@ int reinit(sv_batch* b, int c) {
 }
 
 // Chain-periods per second of `form` on the chains `sample` (run together).
-int time_form(sv_batch* b, const std::vector<int>& sample, int form, double* rate) {
+int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles,
+              double* rate) {
   *rate = 0.0;
   constexpr int kPeriods = 4;
   ResidentSet rs;
@@ -262,7 +271,7 @@ int time_form(sv_batch* b, const std::vector<int>& sample, int form, double* rat
     rc = build_resident(b, sample, &rs);
   } else {
     for (int c : sample) {
-      rc = build_graph_form(b, c, form);
+      rc = build_graph_form(b, c, form, min_tiles);
       if (rc) break;
       graph_chains.push_back(c);
     }
@@ -301,19 +310,27 @@ int autotune(sv_batch* b) {
     const int L = kv.first;
     std::vector<int> sample(kv.second.begin(),
                             kv.second.begin() + std::min<size_t>(8, kv.second.size()));
-    int best = SV_BATCH_PLAIN;
+    int best = SV_BATCH_PLAIN, best_tiles = kDefaultTileRun;
     double best_rate = -1.0;
     for (int f : {SV_BATCH_RESIDENT, SV_BATCH_BLOCK_TC, SV_BATCH_BLOCK_SIMT, SV_BATCH_PLAIN}) {
       if (!form_fits(f, L)) continue;
-      double rate = 0.0;
-      int rc = time_form(b, sample, f, &rate);
-      if (rc) return rc;
-      if (rate > best_rate) {
-        best_rate = rate;
-        best = f;
+      const bool block = f == SV_BATCH_BLOCK_TC || f == SV_BATCH_BLOCK_SIMT;
+      for (int t : kTileRuns) {
+        if (!block && t != kDefaultTileRun) continue;
+        double rate = 0.0;
+        int rc = time_form(b, sample, f, t, &rate);
+        if (rc) return rc;
+        if (rate > best_rate) {
+          best_rate = rate;
+          best = f;
+          best_tiles = t;
+        }
       }
     }
-    for (int c : kv.second) b->form[c] = best;
+    for (int c : kv.second) {
+      b->form[c] = best;
+      b->min_tiles[c] = best_tiles;
+    }
   }
   return SV_OK;
 }
@@ -324,7 +341,7 @@ int setup(sv_batch* b) {
     if (b->form[c] == SV_BATCH_RESIDENT) {
       b->res.push_back(c);
     } else {
-      int rc = build_graph_form(b, c, b->form[c]);
+      int rc = build_graph_form(b, c, b->form[c], b->min_tiles[c]);
       if (rc) return rc;
     }
   }
@@ -425,6 +442,7 @@ int sv_batch_create(sv_batch** out, int device, int n_chains, const int* L,
   }
   if (rc == SV_OK) {
     b->form.assign(n_chains, SV_BATCH_PLAIN);
+    b->min_tiles.assign(n_chains, kDefaultTileRun);
     if (form == SV_BATCH_AUTO) {
       rc = autotune(b);
     } else {

@@ -32,6 +32,8 @@ namespace fsv {
 int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out);
 // Account for periods run through such graphs on the host mirror.
 void ctx_advance(sv_ctx* ctx, int64_t periods);
+// Block passes of later builds keep at least `tiles` tiles per CTA.
+void ctx_set_min_tiles(sv_ctx* ctx, int tiles);
 // (energy density, norm) of periods c0 .. c0+count-1 from the energy ring.
 int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n);
 // Periods the energy ring holds.

@@ -41,6 +41,9 @@ constexpr bool kGateLo = sizeof(R) == 4;
 
 struct LaunchCfg {
   int num_sms = 148;
+  // at least this many tiles per CTA in block passes (0: one wave over the
+  // SMs); batches set it so that several chains' passes share the device
+  int min_tiles_per_cta = 0;
 };
 
 // Grid (blocks of 256 threads) used by the plain gate pass for this L and

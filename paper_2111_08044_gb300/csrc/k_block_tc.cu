@@ -7,10 +7,11 @@
 // evolution (measured: a dissipative drift of the energy density).  The
 // full-magnitude part of the product is therefore accumulated exactly:
 //   - each state row (64 complex = 128 reals) with 2^e_r >= max |x| is cut
-//     into three balanced 8-bit digits at the row's own units,
-//     x = 2^(e_r-7) (s0 + s1/256 + s2/65536), |s| <= 128, each rounded to
-//     nearest (the residual is below 2^-24 of the row's largest entry, as
-//     for FP32 rounding);
+//     into three digits, x = 2^(e_r-7) (s0 + s1/256 + s2/65536): s0 and s1
+//     balanced 8-bit digits at the row's own units (|s| <= 128, rounded to
+//     nearest), s2 the remainder rounded to nearest bf16 (|s2| <= 128; the
+//     residual is below 2^-25 of 2^e_r, finer than FP32 rounding of the
+//     row's largest entry);
 //   - each entry of the fused unitary likewise, u = 2^-7 (u0 + u1/256 +
 //     u2/65536);
 //   - the digits are held as exact bf16 values at their true scale, so the
@@ -42,13 +43,14 @@
 //   warp 9      one thread keeps the TMA producer going: the pass's six
 //               64x64 bf16 digit matrices once, then four 128-row x 128-byte
 //               boxes per tile (cp.async.bulk.tensor.5d, 128-byte swizzle)
-//               into a ring of six box slots; a slot is refilled as soon as
+//               into a ring of seven box slots; a slot is refilled as soon as
 //               the converters hold its rows in registers.
 //   warps 10-11 idle (they complete the third warpgroup for setmaxnreg).
 // Every wait is an mbarrier try_wait loop bounded by a clock budget; on
 // timeout the CTA raises *status, drains its own copies and MMAs, frees
 // TMEM and exits.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -71,15 +73,17 @@ constexpr int kRows = 128;            // tile rows = MMA M = TMEM lanes
 constexpr int kThreads = 384;         // three warpgroups; registers 216 / 232 / 56 a thread
 constexpr uint32_t kTileBytes = kRows * kCols * 8;   // 64 KiB
 constexpr uint32_t kBoxBytes = kRows * 128;           // 16 KiB (one 128-byte column box)
-constexpr int kSlots = 6;                             // input ring: 1.5 tiles of boxes
+constexpr int kSlots = 7;                             // input ring: 1.75 tiles of boxes
 constexpr uint32_t kMatBytes = kCols * kCols * 2;     // one 64 x 64 bf16 matrix
 constexpr uint32_t kWBytes = 6 * kMatBytes;           // Ur, Ui in three digits: 48 KiB
 constexpr uint32_t kOffOut = 0;                       // output staging tile
 constexpr uint32_t kOffW = kOffOut + kTileBytes;
 constexpr uint32_t kOffRing = kOffW + kWBytes;
 constexpr uint32_t kOffMisc = kOffRing + kSlots * kBoxBytes;
-constexpr uint32_t kMiscBytes = 2048;
+constexpr uint32_t kMiscBytes = 1024;
 constexpr uint32_t kSmemBytes = kOffMisc + kMiscBytes + 1024;  // + alignment slack
+static_assert(kSlots <= 8, "barrier block holds at most 8 slots");
+static_assert(kSmemBytes <= 227 * 1024, "dynamic shared memory per CTA");
 // TMEM columns: A (bf16 pairs) in two K-halves of 96 columns: half h at
 // 96 h holds the s0 / s1 / s2 digit planes of the real and imaginary parts
 // for k in [32 h, 32 h + 32) at offsets 0, 16, 32 (real) and 48, 64, 80
@@ -91,18 +95,18 @@ constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 // misc block layout (offsets from kOffMisc)
 enum : uint32_t {
-  kBarFull = 0,      // kSlots x 8: box slot loaded
-  kBarEmpty = 48,    // kSlots x 8: box slot read by the converters
-  kBarW = 96,        // operand block loaded
-  kBarAReady = 104,  // 2 x 8: A half h written
-  kBarAFree = 120,   // 2 x 8: A half h consumed by the MMAs
-  kBarDFull = 136,   // accumulators complete
-  kBarDFree = 144,   // accumulators read out
-  kBarMmaDone = 152,
-  kTmemSlot = 160,
-  kAbort = 164,
+  kBarFull = 0,      // kSlots x 8 (at most 8 slots): box slot loaded
+  kBarEmpty = 64,    // kSlots x 8: box slot read by the converters
+  kBarW = 128,       // operand block loaded
+  kBarAReady = 136,  // 2 x 8: A half h written
+  kBarAFree = 152,   // 2 x 8: A half h consumed by the MMAs
+  kBarDFull = 168,   // accumulators complete
+  kBarDFree = 176,   // accumulators read out
+  kBarMmaDone = 184,
+  kTmemSlot = 192,
+  kAbort = 196,
   kRed = 256,        // 4 x 2 doubles
-  kDiagQ = 512,      // 64 floats: window-window bond part of the diagonal
+  kDiagQ = 512,      // 64 floats (to 768): window-window bond part of the diagonal
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -262,6 +266,20 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
+// Two FP32 values rounded to nearest bf16 (one conversion instruction),
+// packed with `lo` in the low half.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Largest of three FP32 values (one three-input max on sm_100 and later).
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // Two values with at most 8 significant bits each, packed as bf16x2 with
 // `lo` in the low half: their FP32 encodings end in 16 zero bits, so the
 // bf16 values are the high halves (a byte permute, no rounding).
@@ -359,37 +377,38 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     for (long long i = 0; i < my_tiles; ++i) {
-      // box c of tile i is load number g = 4 i + c, in ring slot g mod 6
+      // box c of tile i is load number g = 4 i + c, in ring slot g mod kSlots
       const long long g0 = 4 * i;
       const int s0 = (int)(g0 % kSlots);
       auto slot = [s0](int c) { return s0 + c >= kSlots ? s0 + c - kSlots : s0 + c; };
+      // the row (64 complex) into registers box by box, each slot handed
+      // back to the producer as soon as it is read; exponent 2^e >= max |x|
+      float4 row[32];
+      float m = 0.f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const long long g = g0 + c;
         if (ok) ok = wait_bar(mbase + kBarFull + 8 * slot(c), (uint32_t)((g / kSlots) & 1), abort,
                               status);
-      }
-      if (__any_sync(0xffffffffu, !ok)) break;  // the warp leaves together
-      // the row (64 complex) into registers; exponent 2^e >= max |x|
-      float4 row[32];
-      float m = 0.f;
+        if (__any_sync(0xffffffffu, !ok)) {  // the warp leaves together
+          ok = false;
+          break;
+        }
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        row[q] = *reinterpret_cast<const float4*>(smem + kOffRing + slot(q >> 3) * kBoxBytes +
-                                                  r * 128 + (((q & 7) ^ (r & 7)) << 4));
-        m = fmaxf(m, fmaxf(fmaxf(fabsf(row[q].x), fabsf(row[q].y)),
-                           fmaxf(fabsf(row[q].z), fabsf(row[q].w))));
+        for (int q = 8 * c; q < 8 * c + 8; ++q) {
+          row[q] = *reinterpret_cast<const float4*>(smem + kOffRing + slot(c) * kBoxBytes +
+                                                    r * 128 + (((q & 7) ^ (r & 7)) << 4));
+          m = max3(max3(m, fabsf(row[q].x), fabsf(row[q].y)), fabsf(row[q].z), fabsf(row[q].w));
+        }
+        mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
       }
-      // the slots are no longer needed: let the producer refill them now
-#pragma unroll
-      for (int c = 0; c < 4; ++c) mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
+      if (!ok) break;
       // 2^e >= max |x| (m = f 2^e, f in [0.5, 1)); rows below 2^-100 are
       // cut at that unit (their digits stay normal bf16 numbers)
       int e = -100;
       if (m > 0x1p-100f) frexpf(m, &e);
-      // digit units 2^(e-7), 2^(e-15), 2^(e-23)
-      const uint64_t M0 = f2(magic(e + 16), magic(e + 16)), M1 = f2(magic(e + 8), magic(e + 8)),
-                     M2 = f2(magic(e), magic(e));
+      // digit units 2^(e-7), 2^(e-15); the last digit is the remainder in bf16
+      const uint64_t M0 = f2(magic(e + 16), magic(e + 16)), M1 = f2(magic(e + 8), magic(e + 8));
       for (int h = 0; h < 2 && ok; ++h) {
         if (i >= 1)
           ok = wait_bar(mbase + kBarAFree + 8 * h, (uint32_t)((i - 1) & 1), abort, status);
@@ -410,22 +429,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             float d0[4], d1[4], d2[4];  // re k, im k, re k+1, im k+1
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-              // each digit at most 128 of its unit (8 bits, exact in bf16);
-              // the remainders are exact
+              // the first two digits at most 128 of their unit (8 bits,
+              // exact in bf16); the remainders are exact, and the second
+              // remainder (at most 2^(e-16)) is rounded to bf16 below
               const uint64_t a0 = round_at2(p[t], M0);
               const uint64_t q1 = sub2(p[t], a0);
               const uint64_t a1 = round_at2(q1, M1);
-              const uint64_t a2 = round_at2(sub2(q1, a1), M2);
               f2_split(a0, d0[2 * t], d0[2 * t + 1]);
               f2_split(a1, d1[2 * t], d1[2 * t + 1]);
-              f2_split(a2, d2[2 * t], d2[2 * t + 1]);
+              f2_split(sub2(q1, a1), d2[2 * t], d2[2 * t + 1]);
             }
             r0[s] = pack_bf16x2(d0[0], d0[2]);
             i0[s] = pack_bf16x2(d0[1], d0[3]);
             r1[s] = pack_bf16x2(d1[0], d1[2]);
             i1[s] = pack_bf16x2(d1[1], d1[3]);
-            r2[s] = pack_bf16x2(d2[0], d2[2]);
-            i2[s] = pack_bf16x2(d2[1], d2[3]);
+            r2[s] = cvt_bf16x2(d2[0], d2[2]);
+            i2[s] = cvt_bf16x2(d2[1], d2[3]);
           }
           const uint32_t hb = lane_base + kAHalf * h + 8 * cc;
           tmem_st8(hb + kColR0, r0);
@@ -695,7 +714,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
       }
     } else if (warp == 9 && lane == 0) {
-      // load number g is box (g mod 4) of tile g / 4, into slot g mod 6
+      // load number g is box (g mod 4) of tile g / 4, into slot g mod kSlots
       auto load_box = [&](long long g) {
         const long long t = blockIdx.x + (g >> 2) * gridDim.x;
         const int tlo = (int)(t & ((1ll << (a - kN)) - 1));

@@ -275,6 +275,26 @@ int sv_host_period_gates(int L, const sv_floquet_params *p, int *n_gates,
 int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
                         int *window_lo, int *gate_count, double *unitaries_out);
 
+/*
+ * Block-mode tile layout of each pass (the relabel of Sec. II's qubit
+ * swaps folded into the pass's write; n < L).  *n_passes is in/out as
+ * above.  For pass k, any output may be NULL:
+ *   tile_a[k]                the first state bit of the tile's row bits;
+ *   sigma_out[13k + q]       the output tile bit of input tile bit q (window
+ *                            bits q < n, then min(7, L - n) row bits; -1
+ *                            past the tile);
+ *   rows_out[7k + i]         for the tensor-core pass (n = 6, L >= 13), the
+ *                            tile row bits held by TMEM lane bit i (an
+ *                            invertible map over GF(2); 0 otherwise);
+ *   store_wavefronts[k]      that pass's shared-memory wavefronts per warp
+ *                            store of its relabelled write (2 = free of bank
+ *                            conflicts; 0 if not a tensor-core pass).
+ * Errors: SV_EINVAL.
+ */
+int sv_host_block_layout(int L, const sv_floquet_params *p, int n, int *n_passes,
+                         int *tile_a, int *sigma_out, unsigned char *rows_out,
+                         int *store_wavefronts);
+
 /* ------------------------------------------------------------------ batch
  * Many independent chains (each its own L, parameters and product state)
  * evolved together on one device.  Chains of up to 14 sites can stay in one

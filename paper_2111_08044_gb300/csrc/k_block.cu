@@ -158,6 +158,32 @@ cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStrea
   }
 }
 
+std::string block_tile_layout(int L, int n, int R, int lo, int lo_next, int* a_out,
+                              int8_t* sigma) {
+  const int lo_min = std::min(lo, lo_next);
+  const int delta = std::abs(lo_next - lo);
+  if (delta > R) return "window moves by more than the tile's row bits";
+  const int a = (R == L - n) ? n : std::max(n, std::min(n + lo_min, L - R));
+  if (!(a <= n + lo_min && n + lo_min + delta <= a + R)) return "row bits miss moved sites";
+  for (int q = 0; q < n + R; ++q) {
+    const int p = q < n ? q : a + q - n;
+    const int s = site_at(L, n, lo, p);
+    const int po = pos_of(L, n, lo_next, s);
+    int qo;
+    if (po < n) qo = po;
+    else if (po >= a && po < a + R) qo = po - a + n;
+    else return "site leaves the tile";
+    sigma[q] = (int8_t)qo;
+  }
+  for (int p = 0; p < L; ++p) {
+    const bool in_tile = p < n || (p >= a && p < a + R);
+    if (!in_tile && site_at(L, n, lo, p) != site_at(L, n, lo_next, p))
+      return "layout change outside the tile";
+  }
+  *a_out = a;
+  return std::string();
+}
+
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
                 int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg) {
   *out = nullptr;
@@ -191,33 +217,15 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     const BlockPass& ps = bp->passes[k];
     const int lo = ps.lo;
     const int lo_next = bp->passes[(k + 1) % P].lo;
-    const int lo_min = std::min(lo, lo_next);
-    const int delta = std::abs(lo_next - lo);
-    if (delta > R) return fail("window moves by more than the tile's row bits");
-    int a = (R == L - n) ? n : std::max(n, std::min(n + lo_min, L - R));
-    if (!(a <= n + lo_min && n + lo_min + delta <= a + R)) return fail("row bits miss moved sites");
     PassArgs pa;
     pa.L = L;
     pa.n = n;
     pa.R = R;
-    pa.a = a;
     pa.lo = lo;
     pa.ntiles = ntiles;
-    for (int q = 0; q < n + R; ++q) {
-      const int p = q < n ? q : a + q - n;
-      const int s = site_at(L, n, lo, p);
-      const int po = pos_of(L, n, lo_next, s);
-      int qo;
-      if (po < n) qo = po;
-      else if (po >= a && po < a + R) qo = po - a + n;
-      else return fail("site leaves the tile");
-      pa.sigma[q] = (int8_t)qo;
-    }
-    for (int p = 0; p < L; ++p) {
-      const bool in_tile = p < n || (p >= a && p < a + R);
-      if (!in_tile && site_at(L, n, lo, p) != site_at(L, n, lo_next, p))
-        return fail("layout change outside the tile");
-    }
+    const std::string why = block_tile_layout(L, n, R, lo, lo_next, &pa.a, pa.sigma);
+    if (!why.empty()) return fail(why);
+    if (bp->tensor_cores) block_tc_row_map(pa.sigma, pa.rowvec);
     for (int s : ps.x_sites) {
       const int j = s - lo;
       if (j < 0 || j >= n) return fail("measured site outside window");

@@ -26,10 +26,12 @@
 // Per CTA (one per SM, persistent over tiles), three warpgroups whose
 // register shares are rebalanced with setmaxnreg (168 a thread at launch,
 // 128 x (216 + 232 + 56) in total):
-//   warps 0-3   converters: thread = row = TMEM lane; digits of the row into
-//               TMEM (tcgen05.st) as the A operand, in two K-halves so that
-//               the next tile's conversion overlaps the current tile's MMAs.
-//               Warp 0 also allocates TMEM (512 columns).
+//   warps 0-3   converters: thread = TMEM lane m, which holds tile row r(m)
+//               (a per-pass invertible map over GF(2), chosen so that the
+//               epilogue's staging stores spread over the banks); digits of
+//               the row into TMEM (tcgen05.st) as the A operand, in two
+//               K-halves so that the next tile's conversion overlaps the
+//               current tile's MMAs.  Warp 0 also allocates TMEM (512 columns).
 //   warps 4-7   epilogue: tcgen05.ld of the two accumulators, energy terms
 //               (<X> of window sites in-row; the diagonal part on the natural
 //               layout of the period's last pass), then the fused relabel:
@@ -325,6 +327,15 @@ __device__ __forceinline__ float magic(int q) {
   return __uint_as_float(((uint32_t)(q + 127) << 23) | 0x400000u);
 }
 
+// Tile row held by TMEM lane m: XOR over the set bits i of m of rowvec[i].
+__device__ __forceinline__ int tile_row(const PassArgs& pa, int m) {
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+    if ((m >> i) & 1) r ^= pa.rowvec[i];
+  return r;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     k_block_tc(const __grid_constant__ CUtensorMap tmap_in,
                const __grid_constant__ CUtensorMap tmap_out, PassArgs pa, int* status) {
@@ -373,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (wg == 0) {
     // ------------------------------------------------------------ converters
     asm volatile("setmaxnreg.inc.sync.aligned.u32 216;" ::: "memory");
-    const int r = warp * 32 + lane;  // tile row = TMEM lane
+    const int r = tile_row(pa, warp * 32 + lane);  // the tile row of this TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     for (long long i = 0; i < my_tiles; ++i) {
@@ -381,8 +392,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long g0 = 4 * i;
       const int s0 = (int)(g0 % kSlots);
       auto slot = [s0](int c) { return s0 + c >= kSlots ? s0 + c - kSlots : s0 + c; };
-      // the row (64 complex) into registers box by box, each slot handed
-      // back to the producer as soon as it is read; exponent 2^e >= max |x|
+      // the row (64 complex) into registers box by box as they land;
+      // exponent 2^e >= max |x|
       float4 row[32];
       float m = 0.f;
 #pragma unroll
@@ -400,9 +411,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                     r * 128 + (((q & 7) ^ (r & 7)) << 4));
           m = max3(max3(m, fabsf(row[q].x), fabsf(row[q].y)), fabsf(row[q].z), fabsf(row[q].w));
         }
-        mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
       }
       if (!ok) break;
+      // Hand the four slots back to the producer.  The next TMA load into a
+      // slot writes through the async proxy, so the generic-proxy reads
+      // above are ordered before it by a proxy fence ahead of the release
+      // (without it the copy could overwrite a slot still being read).
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll
+      for (int c = 0; c < 4; ++c) mbar_arrive(mbase + kBarEmpty + 8 * slot(c));
       // 2^e >= max |x| (m = f 2^e, f in [0.5, 1)); rows below 2^-100 are
       // cut at that unit (their digits stay normal bf16 numbers)
       int e = -100;
@@ -464,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ epilogue
     asm volatile("setmaxnreg.inc.sync.aligned.u32 232;" ::: "memory");
     const int q = warp - 4;
-    const int r = q * 32 + lane;  // tile row = TMEM lane
+    const int r = tile_row(pa, q * 32 + lane);  // the tile row of this TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
     const bool elected = q == 0 && lane == 0;  // issues the tile's TMA store
     // Output tile bits: row bit b of this tile goes to output bit sigma[6+b],
@@ -794,6 +811,103 @@ uint16_t bf16_of_int(double v, double scale) {
 bool block_tc_supported(int L, int n) { return n == kN && L >= kN + 7; }
 
 size_t block_tc_w_bytes(int n) { return n == kN ? kWBytes : 0; }
+
+namespace {
+// 8-byte slot (bank pair, 0..15) contributed by output tile bit o to a
+// staging byte address under the 128-byte swizzle: amplitude bits 0-3 are
+// slot bits 0-3, bits 4-6 are XORed into slot bits 1-3, and higher bits only
+// select the 128-byte line.
+int staging_slot_bit(int o) { return o < 4 ? 1 << o : (o < 7 ? 1 << (o - 3) : 0); }
+// Rank over GF(2) of k bit vectors of at most 8 bits.
+int gf2_rank(const int* v, int k) {
+  int piv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int r = 0;
+  for (int i = 0; i < k; ++i) {
+    int x = v[i];
+    for (int b = 7; b >= 0 && x; --b) {
+      if (!((x >> b) & 1)) continue;
+      if (!piv[b]) {
+        piv[b] = x;
+        ++r;
+        break;
+      }
+      x ^= piv[b];
+    }
+  }
+  return r;
+}
+}  // namespace
+
+int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec) {
+  // The 32 lanes of an epilogue warp are TMEM lanes 32q + t; with rows
+  // r(m) = M m over GF(2), the staging slot of lane t's store is linear in
+  // t, and a store takes 2^(5 - rank) wavefronts, where rank is that of the
+  // slot images of M's first five columns (4 at best: two lanes per slot).
+  int v[7];
+  for (int b = 0; b < 7; ++b) v[b] = staging_slot_bit(sigma[kN + b]);
+  auto img = [&](int m) {
+    int x = 0;
+    for (int b = 0; b < 7; ++b)
+      if ((m >> b) & 1) x ^= v[b];
+    return x;
+  };
+  const int reach = std::min(4, gf2_rank(v, 7));
+  // Columns 0-2 keep row bits 0-2 (plus any of rows 3-6): the 8 lanes of
+  // each quarter of a converter LDS.128 then read 8 different 16-byte chunks
+  // of the swizzled box.  Two more columns add at most two image dimensions.
+  int best = -1, best_h = 0;
+  for (int h = 0; h < 4096 && best < reach; ++h) {
+    const int im[3] = {img(1 | ((h & 15) << 3)), img(2 | (((h >> 4) & 15) << 3)),
+                       img(4 | ((h >> 8) << 3))};
+    const int r = std::min(reach, gf2_rank(im, 3) + 2);
+    if (r > best) {
+      best = r;
+      best_h = h;
+    }
+  }
+  int m[7] = {1 | ((best_h & 15) << 3), 2 | (((best_h >> 4) & 15) << 3), 4 | ((best_h >> 8) << 3),
+              0, 0, 0, 0};
+  auto independent = [&](int cand, int k) {
+    int t[8];
+    for (int i = 0; i < k; ++i) t[i] = m[i];
+    t[k] = cand;
+    return gf2_rank(t, k + 1) == k + 1;
+  };
+  auto image_rank = [&](int k, int extra) {
+    int t[8];
+    for (int i = 0; i < k; ++i) t[i] = img(m[i]);
+    t[k] = img(extra);
+    return gf2_rank(t, k + 1);
+  };
+  // the natural columns first, so that a pass without conflicts keeps them
+  int order[127 + 4], no = 0;
+  for (int c : {8, 16, 32, 64}) order[no++] = c;
+  for (int c = 1; c < 128; ++c) order[no++] = c;
+  for (int k = 3; k < 7; ++k) {
+    int pick = 0;
+    if (k < 5) {
+      int have[8];
+      for (int i = 0; i < k; ++i) have[i] = img(m[i]);
+      const int cur = gf2_rank(have, k);
+      if (cur < best)
+        for (int i = 0; i < no && !pick; ++i)
+          if (independent(order[i], k) && image_rank(k, order[i]) > cur) pick = order[i];
+    }
+    for (int i = 0; i < no && !pick; ++i)
+      if (independent(order[i], k)) pick = order[i];
+    m[k] = pick;
+  }
+  int im5[5];
+  for (int i = 0; i < 5; ++i) im5[i] = img(m[i]);
+  int low[3] = {m[0] & 7, m[1] & 7, m[2] & 7};
+  if (gf2_rank(m, 7) != 7 || gf2_rank(low, 3) != 3 || gf2_rank(im5, 5) != best) {
+    for (int i = 0; i < 7; ++i) m[i] = 1 << i;  // not reached; the natural map is always valid
+    for (int i = 0; i < 5; ++i) im5[i] = img(m[i]);
+    best = gf2_rank(im5, 5);
+  }
+  for (int i = 0; i < 7; ++i) rowvec[i] = (uint8_t)m[i];
+  return 1 << (5 - best);
+}
 
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
   // six K-major 64 x 64 bf16 digit matrices Ur0, Ur1, Ur2, Ui0, Ui1, Ui2

@@ -1009,4 +1009,36 @@ int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
   return SV_OK;
 }
 
+int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes,
+                         int* tile_a, int* sigma_out, unsigned char* rows_out,
+                         int* store_wavefronts) {
+  if (!p || !n_passes) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  if (n < 2 || n > 7 || n >= L) return SV_EINVAL;
+  auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
+  auto plan = fsv::fusion_plan(L, gates, n);
+  const int P = (int)plan.size();
+  const int cap = *n_passes;
+  *n_passes = P;
+  if (!tile_a && !sigma_out && !rows_out && !store_wavefronts) return SV_OK;
+  if (cap < P) return SV_EINVAL;
+  const int R = std::min(7, L - n);
+  const bool tc = n == 6 && R == 7;
+  for (int k = 0; k < P; ++k) {
+    int a = 0;
+    int8_t sig[16] = {};
+    if (!fsv::block_tile_layout(L, n, R, plan[k].lo, plan[(k + 1) % P].lo, &a, sig).empty())
+      return SV_EINVAL;
+    uint8_t rows[7] = {1, 2, 4, 8, 16, 32, 64};
+    const int wf = tc ? fsv::block_tc_row_map(sig, rows) : 0;
+    if (tile_a) tile_a[k] = a;
+    if (sigma_out)
+      for (int q = 0; q < 13; ++q) sigma_out[13 * k + q] = q < n + R ? sig[q] : -1;
+    if (rows_out)
+      for (int i = 0; i < 7; ++i) rows_out[7 * k + i] = tc ? rows[i] : 0;
+    if (store_wavefronts) store_wavefronts[k] = wf;
+  }
+  return SV_OK;
+}
+
 }  // extern "C"

@@ -35,6 +35,9 @@ struct PassArgs {
   float cx[8] = {};          // coefficient per window-local bit
   int diag = 0;              // measure diagonal part + norm (output is natural layout)
   int8_t sigma[16] = {};     // output tile bit of input tile bit q
+  // tensor-core pass: TMEM lane m holds tile row XOR over set bits i of m
+  // of rowvec[i] (an invertible map, chosen against staging bank conflicts)
+  uint8_t rowvec[7] = {1, 2, 4, 8, 16, 32, 64};
   const float2* U = nullptr; // fused unitary, FP32, row-major 2^n x 2^n
   const void* W = nullptr;   // tensor-core operand block of this pass
   void* psi = nullptr;       // state (set at launch)
@@ -62,6 +65,11 @@ struct BlockPlan {
   int* d_status = nullptr;     // raised by a pass whose bounded wait gave up
 };
 
+// Tile of the pass moving the window from lo to lo_next: its row bits start
+// at position *a_out, and input tile bit q (window bits 0..n-1, then R row
+// bits) goes to output tile bit sigma[q].  Empty on success, else the reason.
+std::string block_tile_layout(int L, int n, int R, int lo, int lo_next, int* a_out,
+                              int8_t* sigma);
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
                 int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg);
 void block_info(const BlockPlan* bp, int* passes, int* launches);
@@ -90,6 +98,11 @@ size_t block_tc_map_bytes();
 int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out);
 // Bytes of the tensor-core operand block of one pass, and its host layout.
 size_t block_tc_w_bytes(int n);
+// Row map of a tensor-core pass (n = 6, R = 7) for its relabel sigma: keeps
+// the converters' 128-byte-swizzled row reads conflict-free and spreads each
+// epilogue warp's staging stores over as many banks as sigma allows.
+// Returns the staging wavefronts per warp store (2 is conflict-free).
+int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec);
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);
 
 }  // namespace fsv

@@ -161,3 +161,79 @@ def test_batch_host_checks(svlib):
     assert svlib.sv_batch_create(ctypes.byref(b), 0, 0, None, p, None, None, 0, -1,
                                  None) == capi.SV_EINVAL
     assert not b.value
+
+
+def _block_layout(svlib, L, n):
+    p, _ = capi.make_params()
+    cnt = ctypes.c_int(64)
+    lo = (ctypes.c_int * 64)()
+    assert svlib.sv_host_fusion_plan(L, ctypes.byref(p), n, ctypes.byref(cnt), lo, None, None) == 0
+    P = cnt.value
+    a = np.zeros(64, np.int32)
+    sig = np.zeros(64 * 13, np.int32)
+    rows = np.zeros(64 * 7, np.uint8)
+    wf = np.zeros(64, np.int32)
+    c2 = ctypes.c_int(64)
+    assert svlib.sv_host_block_layout(L, ctypes.byref(p), n, ctypes.byref(c2),
+                                      a.ctypes.data_as(capi._ip), sig.ctypes.data_as(capi._ip),
+                                      rows.ctypes.data, wf.ctypes.data_as(capi._ip)) == 0
+    assert c2.value == P
+    return [lo[k] for k in range(P)], a[:P], sig[:13 * P].reshape(P, 13), rows[:7 * P].reshape(P, 7), wf[:P]
+
+
+def _site_position(L, n, lo, s):
+    # window sites on the lowest n bits, sites below it next, the rest in place
+    if lo <= s < lo + n:
+        return s - lo
+    return n + s if s < lo else s
+
+
+@pytest.mark.parametrize("L", [13, 20, 26, 30, 34])
+def test_block_tile_layout_and_row_map(svlib, L):
+    """Each pass's relabel sigma follows the window layout rule; the
+    tensor-core row map is invertible, keeps the converter's swizzled row
+    reads conflict-free, and its reported staging wavefronts equal a
+    brute-force bank count that never exceeds the natural order's."""
+    n, R = 6, min(7, L - 6)
+    los, a, sig, rows, wf = _block_layout(svlib, L, n)
+    P = len(los)
+    for k in range(P):
+        lo, lo_next = los[k], los[(k + 1) % P]
+        tile_pos = list(range(n)) + [a[k] + b for b in range(R)]
+        site_of = {_site_position(L, n, lo, s): s for s in range(L)}
+        for q, pos in enumerate(tile_pos):
+            out_pos = _site_position(L, n, lo_next, site_of[pos])
+            want = out_pos if out_pos < n else tile_pos.index(out_pos)
+            assert sig[k, q] == want, (k, q)
+        if R < 7:
+            assert wf[k] == 0 and not rows[k].any()
+            continue
+        rmap = [0] * 128
+        for m in range(128):
+            for i in range(7):
+                if (m >> i) & 1:
+                    rmap[m] ^= int(rows[k, i])
+        assert sorted(rmap) == list(range(128))
+        # converter: the 8 lanes of each quarter-warp read 8 different 16-byte chunks
+        for m0 in range(0, 128, 8):
+            assert len({rmap[m] & 7 for m in range(m0, m0 + 8)}) == 8
+
+        def wavefronts(rowmap):
+            worst = 0
+            for q in range(4):
+                for c in (0, 21, 63):
+                    slots = {}
+                    for t in range(32):
+                        y = c | (rowmap[32 * q + t] << n)
+                        yo = sum(((y >> b) & 1) << int(sig[k, b]) for b in range(13))
+                        byte = 8 * yo
+                        byte ^= ((byte >> 7) & 7) << 4
+                        slots.setdefault((byte >> 3) & 15, set()).add(byte)
+                    worst = max(worst, max(len(v) for v in slots.values()))
+            return worst
+        got = wavefronts(rmap)
+        assert got == wf[k], (k, got, wf[k])
+        assert got <= wavefronts(list(range(128)))
+    if L == 30:
+        # the two relabels that scattered rows across the banks are fixed
+        assert wf[4] == 4 and wf[5] == 2

@@ -97,3 +97,18 @@ def test_j0_closed_form_full_size(svlib, L, mode, periods):
     e, n = _gpu_energies(cfg, mode, periods)
     np.testing.assert_allclose(e, _j0_closed_form(cfg, periods), atol=1e-5, rtol=0)
     assert np.all(np.abs(n - 1.0) < 1e-5)
+
+
+def test_tensor_core_pass_is_deterministic_L30(svlib):
+    """Two runs of the same L = 30 evolution give bit-identical energies and
+    norms.  Every buffer the tensor-core pass hands between roles (input ring
+    slots, TMEM operands and accumulators, the staging tile) is released only
+    after its readers are done, including the proxy fence between the
+    converters' reads of a ring slot and the next TMA load into it; a missing
+    hand-over shows up here as run-to-run differences."""
+    cfg = inputs.ChainConfig(L=30, seed=4)
+    e1, n1 = _gpu_energies(cfg, "block", 3)
+    e2, n2 = _gpu_energies(cfg, "block", 3)
+    assert np.array_equal(e1, e2), (e1, e2)
+    assert np.array_equal(n1, n2), (n1, n2)
+    assert np.all(np.abs(n1 - 1.0) < 3e-6), n1

@@ -288,12 +288,15 @@ int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
  *                            invertible map over GF(2); 0 otherwise);
  *   store_wavefronts[k]      that pass's shared-memory wavefronts per warp
  *                            store of its relabelled write (2 = free of bank
- *                            conflicts; 0 if not a tensor-core pass).
+ *                            conflicts; 0 if not a tensor-core pass);
+ *   x_sites_out[k]           bit j set if the pass measures <X> of window
+ *                            site window_lo + j (each site once per period,
+ *                            in the pass holding its last gate).
  * Errors: SV_EINVAL.
  */
 int sv_host_block_layout(int L, const sv_floquet_params *p, int n, int *n_passes,
                          int *tile_a, int *sigma_out, unsigned char *rows_out,
-                         int *store_wavefronts);
+                         int *store_wavefronts, int *x_sites_out);
 
 /* ------------------------------------------------------------------ batch
  * Many independent chains (each its own L, parameters and product state)

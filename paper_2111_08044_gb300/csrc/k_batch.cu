@@ -29,6 +29,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int L = ch.L;
   const uint32_t n = 1u << L;
   const long long p0 = *counter;
+  // the chain's coefficients in FP32 once, so that the per-amplitude
+  // measurement below runs no FP64 instruction
+  __shared__ float s_cz[kResidentMaxL], s_cx[kResidentMaxL];
+  if (threadIdx.x < (unsigned)L) {
+    s_cz[threadIdx.x] = (float)ch.cz[threadIdx.x];
+    s_cx[threadIdx.x] = (float)ch.cx[threadIdx.x];
+  }
+  const float Jf = (float)ch.J;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sp[i] = ch.psi[i];
   __syncthreads();
   __shared__ double se[kThreads / 32], sn[kThreads / 32];
@@ -69,22 +77,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncthreads();
     }
     // <H0> and the norm of the period's final state (natural layout)
-    double e = 0.0, nn = 0.0;
+    // per-thread sums over its amplitudes, compensated (Kahan) in FP32
+    float es = 0.f, ec = 0.f, ns = 0.f, nc = 0.f;
     for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) {
       const float2 v = sp[x];
       const float pr = cabs2(v);
       float d = 0.f;
       for (int i = 0; i < L; ++i) {
         const float zi = ((x >> i) & 1) ? -1.f : 1.f;
-        d += (float)ch.cz[i] * zi;
-        if (i + 1 < L) d += (float)ch.J * zi * (((x >> (i + 1)) & 1) ? -1.f : 1.f);
+        d += s_cz[i] * zi;
+        if (i + 1 < L) d += Jf * zi * (((x >> (i + 1)) & 1) ? -1.f : 1.f);
       }
       float ex = 0.f;
       for (int i = 0; i < L; ++i)
-        if (!((x >> i) & 1)) ex += 2.f * (float)ch.cx[i] * cdotre(v, sp[x | (1u << i)]);
-      e += (double)(pr * d + ex);
-      nn += (double)pr;
+        if (!((x >> i) & 1)) ex += 2.f * s_cx[i] * cdotre(v, sp[x | (1u << i)]);
+      const float ye = (pr * d + ex) - ec, te = es + ye;
+      ec = (te - es) - ye;
+      es = te;
+      const float yn = pr - nc, tn = ns + yn;
+      nc = (tn - ns) - yn;
+      ns = tn;
     }
+    double e = (double)es - (double)ec, nn = (double)ns - (double)nc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       e += __shfl_xor_sync(0xffffffffu, e, o);

@@ -240,6 +240,11 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
       pa.ep.cz_first = obs.cz[0];
       pa.ep.cz_last = obs.cz[L - 1];
       pa.ep.cz_bulk = L >= 3 ? obs.cz[1] : 0.0;
+      pa.diag_f[0] = (float)pa.ep.J;
+      pa.diag_f[1] = (float)pa.ep.cz_bulk;
+      pa.diag_f[2] = (float)pa.ep.cz_first;
+      pa.diag_f[3] = (float)pa.ep.cz_last;
+      pa.diag_f[4] = (float)(pa.ep.cz_bulk * (L - 2) + pa.ep.cz_first + pa.ep.cz_last);
     }
     if (pa.x_mask || pa.diag) pa.slot = slot++;
     bp->args.push_back(pa);

@@ -25,7 +25,8 @@
 //
 // Per CTA (one per SM, persistent over tiles), three warpgroups whose
 // register shares are rebalanced with setmaxnreg (168 a thread at launch,
-// 128 x (216 + 232 + 56) in total):
+// 128 x (216 + 232 + 56) in total, 224 + 224 + 56 for passes that measure
+// nothing):
 //   warps 0-3   converters: thread = TMEM lane m, which holds tile row r(m)
 //               (a per-pass invertible map over GF(2), chosen so that the
 //               epilogue's staging stores spread over the banks); digits of
@@ -336,6 +337,14 @@ __device__ __forceinline__ int tile_row(const PassArgs& pa, int m) {
   return r;
 }
 
+// kX: the pass measures <X> of window sites; kDiag: it measures the
+// diagonal part and the norm (the period's last pass).  A pass whose CTAs
+// run many tiles takes the instance of its combination, whose epilogue is
+// compiled (and register-allocated) for only the work it does; short passes
+// (small chains, many of them at once in a batch) all take the generic
+// instance (kGeneric, flags read at run time), so that SMs switching between
+// their CTAs keep one kernel's code in the instruction cache.
+template <bool kGeneric, bool kX, bool kDiag>
 __global__ void __launch_bounds__(kThreads, 1)
     k_block_tc(const __grid_constant__ CUtensorMap tmap_in,
                const __grid_constant__ CUtensorMap tmap_out, PassArgs pa, int* status) {
@@ -383,7 +392,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int wg = warp >> 2;
   if (wg == 0) {
     // ------------------------------------------------------------ converters
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 216;" ::: "memory");
+    // register shares: 216 / 232 / 56 when the epilogue measures, else
+    // 224 / 224 / 56 (both sum to the 168 x 3 a thread the CTA launched with)
+    if constexpr (kGeneric || kX || kDiag)
+      asm volatile("setmaxnreg.inc.sync.aligned.u32 216;" ::: "memory");
+    else asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
     const int r = tile_row(pa, warp * 32 + lane);  // the tile row of this TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
@@ -479,7 +492,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (wg == 1) {
     // ------------------------------------------------------------ epilogue
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 232;" ::: "memory");
+    if constexpr (kGeneric || kX || kDiag)
+      asm volatile("setmaxnreg.inc.sync.aligned.u32 232;" ::: "memory");
+    else asm volatile("setmaxnreg.inc.sync.aligned.u32 224;" ::: "memory");
     const int q = warp - 4;
     const int r = tile_row(pa, q * 32 + lane);  // the tile row of this TMEM lane
     const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
@@ -504,9 +519,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     // bits, window neighbours counted at 0) and Q[c] = 4 J sum over adjacent
     // window pairs of c_j c_k, a 64-entry table shared by all rows.
     float* diag_q = reinterpret_cast<float*>(misc + kDiagQ);
+    const bool do_x = kGeneric ? pa.x_mask != 0 : kX;
+    const bool do_diag = kGeneric ? pa.diag != 0 : kDiag;
     // global bit of window bit j in the output
     auto gcol = [&](int j) { return pa.sigma[j] < kN ? pa.sigma[j] : a + pa.sigma[j] - kN; };
-    if (pa.diag) {
+    if (do_diag) {
       if (r < kCols) {
         float qv = 0.f;
         for (int j = 0; j < kN; ++j)
@@ -519,7 +536,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const float sc = (float)renorm_scale(pa.ep.rn);
     const uint64_t sc2 = f2(sc, sc);
-    double eacc = 0.0, nacc = 0.0;
+    // per-thread energy and norm over its tiles: compensated FP32 sums
+    // (Kahan), so that no FP64 instruction runs per tile
+    float es_s = 0.f, es_c = 0.f, ns_s = 0.f, ns_c = 0.f;
     for (long long i = 0; i < my_tiles; ++i) {
       const bool ok = wait_bar(mbase + kBarDFull, (uint32_t)(i & 1), abort, status);
       if (!epilogue_all_ok(ok)) break;  // the four epilogue warps leave together
@@ -549,10 +568,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       mbar_arrive(mbase + kBarDFree);  // the accumulators may be overwritten
       float es = 0.f, ns = 0.f;
-      if (pa.x_mask) {
+      if (do_x) {
         // <X_j> part of the row: 2 sum over c with bit j clear of
-        // re_c re_c' + im_c im_c', c' = c + 2^j; for j >= 1 two neighbouring
-        // columns go through one packed FMA
+        // re_c re_c' + im_c im_c', c' = c + 2^j, for the bits this pass
+        // measures; for j >= 1 two neighbouring columns go through one
+        // packed FMA
 #pragma unroll
         for (int j = 0; j < kN; ++j) {
           if (!((pa.x_mask >> j) & 1)) continue;
@@ -566,16 +586,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             sj = t0 + t1;
           } else {
-            uint64_t acc = f2(0.f, 0.f);
+            uint64_t xacc = f2(0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < kCols; c += 2) {
               if ((c >> j) & 1) continue;
               const int c2 = c + (1 << j);
-              acc = fma2(f2(re[c], re[c + 1]), f2(re[c2], re[c2 + 1]), acc);
-              acc = fma2(f2(im[c], im[c + 1]), f2(im[c2], im[c2 + 1]), acc);
+              xacc = fma2(f2(re[c], re[c + 1]), f2(re[c2], re[c2 + 1]), xacc);
+              xacc = fma2(f2(im[c], im[c + 1]), f2(im[c2], im[c2 + 1]), xacc);
             }
             float lo, hi;
-            f2_split(acc, lo, hi);
+            f2_split(xacc, lo, hi);
             sj = lo + hi;
           }
           es += 2.f * pa.cx[j] * sj;
@@ -584,40 +604,68 @@ __global__ void __launch_bounds__(kThreads, 1)
       const long long t = blockIdx.x + i * gridDim.x;
       const uint32_t tlo = (uint32_t)(t & ((1ll << (a - kN)) - 1));
       const uint32_t thi = (uint32_t)(t >> (a - kN));
-      if (pa.diag) {
+      if (do_diag) {
         // the period's last pass writes the natural layout: measure the
         // diagonal part and the norm on the amplitudes' natural indices
         const uint64_t tbase = ((uint64_t)tlo << kN) | ((uint64_t)thi << (a + 7));
         const uint64_t x0 = tbase | (yrow & (kCols - 1)) | ((uint64_t)(yrow >> kN) << a);
+        // FP32 coefficients rounded on the host (no FP64 work per tile)
         Diag<float> dg;
-        dg.init(pa.ep, pa.L);
+        dg.L = pa.L;
+        dg.J = pa.diag_f[0];
+        dg.cz_bulk = pa.diag_f[1];
+        dg.cz_first = pa.diag_f[2];
+        dg.cz_last = pa.diag_f[3];
+        dg.czsum = pa.diag_f[4];
+        dg.zzmask = (1ull << (pa.L - 1)) - 1;
+        dg.bulkmask = ((1ull << pa.L) - 1) & ~1ull & ~(1ull << (pa.L - 1));
         const float h0 = dg(x0);
         float lin[kN];
 #pragma unroll
         for (int j = 0; j < kN; ++j) {
           const int g = gcol(j);
           float nb = 0.f;  // sum of the neighbours' z at c = 0
-          if (g >= 1) nb += 1.f - 2.f * (float)((x0 >> (g - 1)) & 1);
-          if (g <= pa.L - 2) nb += 1.f - 2.f * (float)((x0 >> (g + 1)) & 1);
+          if (g >= 1) nb += ((x0 >> (g - 1)) & 1) ? -1.f : 1.f;
+          if (g <= pa.L - 2) nb += ((x0 >> (g + 1)) & 1) ? -1.f : 1.f;
           const float czg = g == 0 ? dg.cz_first : (g == pa.L - 1 ? dg.cz_last : dg.cz_bulk);
           lin[j] = -2.f * (czg + dg.J * nb);
         }
-        // Gray-code walk over c: one window bit flips per step
-        float hl = h0;
+        // h(x_c) = h0 + L(c) + Q[c] with L(c) = sum_j c_j lin_j.  The row is
+        // taken in pairs (c, c + 1) = (2k, 2k + 1), k in Gray-code order, so
+        // W = (L(2k), L(2k) + lin_0) changes by one lin per step; packed,
+        // sum_c p_c h = h0 S + sum_k P_k . (W_k + Q_k), S = sum_c p_c.
+        float w_lo = 0.f, w_hi = lin[0];
+        uint64_t tot = f2(0.f, 0.f), acc = tot;
+        const uint64_t* q2 = reinterpret_cast<const uint64_t*>(diag_q);
 #pragma unroll
-        for (int g = 0; g < kCols; ++g) {
-          const int c = g ^ (g >> 1);
+        for (int g = 0; g < kCols / 2; ++g) {
+          const int k = g ^ (g >> 1);
           if (g > 0) {
-            const int j = low_bit(g);
-            hl += ((c >> j) & 1) ? lin[j] : -lin[j];
+            const int b = low_bit(g);  // pair bit b is window bit b + 1
+            const float d = ((k >> b) & 1) ? lin[b + 1] : -lin[b + 1];
+            w_lo += d;
+            w_hi += d;
           }
-          const float p = re[c] * re[c] + im[c] * im[c];
-          ns += p;
-          es += p * (hl + diag_q[c]);
+          const uint64_t rr = f2(re[2 * k], re[2 * k + 1]), ii = f2(im[2 * k], im[2 * k + 1]);
+          const uint64_t p = fma2(rr, rr, mul2(ii, ii));
+          tot = add2(tot, p);
+          acc = fma2(p, add2(f2(w_lo, w_hi), q2[k]), acc);
         }
+        float t_lo, t_hi, a_lo, a_hi;
+        f2_split(tot, t_lo, t_hi);
+        f2_split(acc, a_lo, a_hi);
+        const float S = t_lo + t_hi;
+        ns += S;
+        es += fmaf(h0, S, a_lo + a_hi);
       }
-      eacc += (double)es;
-      nacc += (double)ns;
+      {
+        const float ye = es - es_c, te = es_s + ye;
+        es_c = (te - es_s) - ye;
+        es_s = te;
+        const float yn = ns - ns_c, tn = ns_s + yn;
+        ns_c = (tn - ns_s) - yn;
+        ns_s = tn;
+      }
       // the staging tile is free once the previous tile's store has read it
       if (elected) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       epilogue_sync();
@@ -644,6 +692,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (elected) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     // energy partials of this CTA (fixed order)
     if (pa.partial) {
+      double eacc = (double)es_s - (double)es_c, nacc = (double)ns_s - (double)ns_c;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
@@ -839,10 +888,11 @@ int gf2_rank(const int* v, int k) {
 }  // namespace
 
 int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec) {
-  // The 32 lanes of an epilogue warp are TMEM lanes 32q + t; with rows
-  // r(m) = M m over GF(2), the staging slot of lane t's store is linear in
-  // t, and a store takes 2^(5 - rank) wavefronts, where rank is that of the
-  // slot images of M's first five columns (4 at best: two lanes per slot).
+  // The 32 lanes of an epilogue warp are TMEM lanes 32q + t, and a 64-bit
+  // shared store is served per half-warp (lanes 0-15, then 16-31).  With
+  // rows r(m) = M m over GF(2) the staging slot of lane t's store is linear
+  // in t, so each half takes 2^(4 - rank) wavefronts, where rank is that of
+  // the slot images of M's first four columns (4 at best: one lane a slot).
   int v[7];
   for (int b = 0; b < 7; ++b) v[b] = staging_slot_bit(sigma[kN + b]);
   auto img = [&](int m) {
@@ -852,61 +902,56 @@ int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec) {
     return x;
   };
   const int reach = std::min(4, gf2_rank(v, 7));
-  // Columns 0-2 keep row bits 0-2 (plus any of rows 3-6): the 8 lanes of
-  // each quarter of a converter LDS.128 then read 8 different 16-byte chunks
-  // of the swizzled box.  Two more columns add at most two image dimensions.
-  int best = -1, best_h = 0;
-  for (int h = 0; h < 4096 && best < reach; ++h) {
-    const int im[3] = {img(1 | ((h & 15) << 3)), img(2 | (((h >> 4) & 15) << 3)),
-                       img(4 | ((h >> 8) << 3))};
-    const int r = std::min(reach, gf2_rank(im, 3) + 2);
-    if (r > best) {
-      best = r;
-      best_h = h;
-    }
-  }
-  int m[7] = {1 | ((best_h & 15) << 3), 2 | (((best_h >> 4) & 15) << 3), 4 | ((best_h >> 8) << 3),
-              0, 0, 0, 0};
+  int m[7] = {0, 0, 0, 0, 0, 0, 0};
   auto independent = [&](int cand, int k) {
     int t[8];
     for (int i = 0; i < k; ++i) t[i] = m[i];
     t[k] = cand;
     return gf2_rank(t, k + 1) == k + 1;
   };
-  auto image_rank = [&](int k, int extra) {
-    int t[8];
-    for (int i = 0; i < k; ++i) t[i] = img(m[i]);
-    t[k] = img(extra);
-    return gf2_rank(t, k + 1);
-  };
   // the natural columns first, so that a pass without conflicts keeps them
   int order[127 + 4], no = 0;
   for (int c : {8, 16, 32, 64}) order[no++] = c;
   for (int c = 1; c < 128; ++c) order[no++] = c;
-  for (int k = 3; k < 7; ++k) {
-    int pick = 0;
-    if (k < 5) {
-      int have[8];
-      for (int i = 0; i < k; ++i) have[i] = img(m[i]);
-      const int cur = gf2_rank(have, k);
-      if (cur < best)
-        for (int i = 0; i < no && !pick; ++i)
-          if (independent(order[i], k) && image_rank(k, order[i]) > cur) pick = order[i];
+  // Columns 0-2 keep row bits 0-2 (plus any of rows 3-6): the 8 lanes of
+  // each quarter of a converter LDS.128 then read 8 different 16-byte chunks
+  // of the swizzled box.  Column 3 is free.
+  int best = -1;
+  int bm[4] = {1, 2, 4, 8};
+  for (int h = 0; h < 4096 && best < reach; ++h) {
+    m[0] = 1 | ((h & 15) << 3);
+    m[1] = 2 | (((h >> 4) & 15) << 3);
+    m[2] = 4 | ((h >> 8) << 3);
+    for (int i = 0; i < no && best < reach; ++i) {
+      if (!independent(order[i], 3)) continue;
+      const int im[4] = {img(m[0]), img(m[1]), img(m[2]), img(order[i])};
+      const int r = gf2_rank(im, 4);
+      if (r > best) {
+        best = r;
+        bm[0] = m[0];
+        bm[1] = m[1];
+        bm[2] = m[2];
+        bm[3] = order[i];
+      }
     }
+  }
+  for (int i = 0; i < 4; ++i) m[i] = bm[i];
+  for (int k = 4; k < 7; ++k) {
+    int pick = 0;
     for (int i = 0; i < no && !pick; ++i)
       if (independent(order[i], k)) pick = order[i];
     m[k] = pick;
   }
-  int im5[5];
-  for (int i = 0; i < 5; ++i) im5[i] = img(m[i]);
+  int im4[4];
+  for (int i = 0; i < 4; ++i) im4[i] = img(m[i]);
   int low[3] = {m[0] & 7, m[1] & 7, m[2] & 7};
-  if (gf2_rank(m, 7) != 7 || gf2_rank(low, 3) != 3 || gf2_rank(im5, 5) != best) {
+  if (gf2_rank(m, 7) != 7 || gf2_rank(low, 3) != 3 || gf2_rank(im4, 4) != best) {
     for (int i = 0; i < 7; ++i) m[i] = 1 << i;  // not reached; the natural map is always valid
-    for (int i = 0; i < 5; ++i) im5[i] = img(m[i]);
-    best = gf2_rank(im5, 5);
+    for (int i = 0; i < 4; ++i) im4[i] = img(m[i]);
+    best = gf2_rank(im4, 4);
   }
   for (int i = 0; i < 7; ++i) rowvec[i] = (uint8_t)m[i];
-  return 1 << (5 - best);
+  return 2 << (4 - best);
 }
 
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
@@ -971,8 +1016,17 @@ int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
 size_t block_tc_map_bytes() { return 2 * sizeof(CUtensorMap); }
 
 cudaError_t block_tc_prepare() {
-  return cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kSmemBytes);
+  const void* fns[5] = {(const void*)k_block_tc<true, false, false>,
+                        (const void*)k_block_tc<false, false, false>,
+                        (const void*)k_block_tc<false, true, false>,
+                        (const void*)k_block_tc<false, false, true>,
+                        (const void*)k_block_tc<false, true, true>};
+  for (const void* f : fns) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int* status,
@@ -981,7 +1035,19 @@ cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int*
   p.psi = psi;
   alignas(64) CUtensorMap maps[2];
   std::memcpy(maps, map, sizeof(maps));
-  k_block_tc<<<grid, kThreads, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+  constexpr long long kMinTilesSpecialised = 32;  // tiles per CTA
+  const long long per_cta = (p.ntiles + grid - 1) / grid;
+  const dim3 g(grid), b(kThreads);
+  if (per_cta < kMinTilesSpecialised)
+    k_block_tc<true, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+  else if (p.diag && p.x_mask)
+    k_block_tc<false, true, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+  else if (p.diag)
+    k_block_tc<false, false, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+  else if (p.x_mask)
+    k_block_tc<false, true, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+  else
+    k_block_tc<false, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
   return cudaGetLastError();
 }
 

@@ -1011,7 +1011,7 @@ int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
 
 int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes,
                          int* tile_a, int* sigma_out, unsigned char* rows_out,
-                         int* store_wavefronts) {
+                         int* store_wavefronts, int* x_sites_out) {
   if (!p || !n_passes) return SV_EINVAL;
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
   if (n < 2 || n > 7 || n >= L) return SV_EINVAL;
@@ -1020,7 +1020,7 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
   const int P = (int)plan.size();
   const int cap = *n_passes;
   *n_passes = P;
-  if (!tile_a && !sigma_out && !rows_out && !store_wavefronts) return SV_OK;
+  if (!tile_a && !sigma_out && !rows_out && !store_wavefronts && !x_sites_out) return SV_OK;
   if (cap < P) return SV_EINVAL;
   const int R = std::min(7, L - n);
   const bool tc = n == 6 && R == 7;
@@ -1037,6 +1037,11 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
     if (rows_out)
       for (int i = 0; i < 7; ++i) rows_out[7 * k + i] = tc ? rows[i] : 0;
     if (store_wavefronts) store_wavefronts[k] = wf;
+    if (x_sites_out) {
+      int mask = 0;
+      for (int site : plan[k].x_sites) mask |= 1 << (site - plan[k].lo);
+      x_sites_out[k] = mask;
+    }
   }
   return SV_OK;
 }

@@ -11,10 +11,11 @@
 // independent branches.
 //
 // The autotuner (form SV_BATCH_AUTO) times every form that fits a distinct
-// L on up to eight of its chains, run together for four periods through the
-// same kind of graph (block forms with 4, 8 or 16 tiles per CTA at least),
-// and keeps the fastest (most chain-periods per second) for all chains of
-// that L.
+// L, run together for four periods through the same kind of graph (block
+// forms with 4, 8 or 16 tiles per CTA at least), and keeps the fastest (most
+// chain-periods per second) for all chains of that L.  The resident form is
+// timed on all chains of that L (one CTA each, so its rate grows with their
+// number); the others, which fill the device with one chain, on up to eight.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -259,23 +260,25 @@ int reinit(sv_batch* b, int c) {
   return SV_OK;
 }
 
-// Chain-periods per second of `form` on the chains `sample` (run together).
-int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles,
-              double* rate) {
+// Chain-periods per second of the chains `sample` run together, chain
+// sample[i] in form forms[i] (block forms with at least tiles[i] tiles per
+// CTA).  The trial moves the states; they are initialised again after it.
+int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<int>& forms,
+               const std::vector<int>& tiles, double* rate) {
   *rate = 0.0;
   constexpr int kPeriods = 4;
   ResidentSet rs;
-  std::vector<int> graph_chains;
+  std::vector<int> graph_chains, res_chains;
   int rc = SV_OK;
-  if (form == SV_BATCH_RESIDENT) {
-    rc = build_resident(b, sample, &rs);
-  } else {
-    for (int c : sample) {
-      rc = build_graph_form(b, c, form, min_tiles);
-      if (rc) break;
-      graph_chains.push_back(c);
+  for (size_t i = 0; i < sample.size() && rc == SV_OK; ++i) {
+    if (forms[i] == SV_BATCH_RESIDENT) {
+      res_chains.push_back(sample[i]);
+    } else {
+      rc = build_graph_form(b, sample[i], forms[i], tiles[i]);
+      graph_chains.push_back(sample[i]);
     }
   }
+  if (rc == SV_OK) rc = build_resident(b, res_chains, &rs);
   cudaGraphExec_t ge = nullptr;
   if (rc == SV_OK) rc = make_graph(b, graph_chains, &rs, kPeriods, &ge);
   if (rc == SV_OK) {
@@ -295,12 +298,17 @@ int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_til
   }
   if (ge) cudaGraphExecDestroy(ge);
   rs.release();
-  // the trial moved the states: start them again
   for (int c : sample) {
     int r2 = reinit(b, c);
     if (rc == SV_OK) rc = r2;
   }
   return rc;
+}
+
+int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles,
+              double* rate) {
+  return time_forms(b, sample, std::vector<int>(sample.size(), form),
+                    std::vector<int>(sample.size(), min_tiles), rate);
 }
 
 int autotune(sv_batch* b) {
@@ -317,8 +325,11 @@ int autotune(sv_batch* b) {
       const bool block = f == SV_BATCH_BLOCK_TC || f == SV_BATCH_BLOCK_SIMT;
       for (int t : kTileRuns) {
         if (!block && t != kDefaultTileRun) continue;
+        // a resident chain uses one CTA, so its form scales with the chain
+        // count up to the SM count: it is timed on every chain of this L;
+        // the other forms fill the device with one chain's passes
         double rate = 0.0;
-        int rc = time_form(b, sample, f, t, &rate);
+        int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, t, &rate);
         if (rc) return rc;
         if (rate > best_rate) {
           best_rate = rate;

@@ -34,6 +34,7 @@ struct PassArgs {
   uint32_t x_mask = 0;       // window-local bits whose <X> this pass measures
   float cx[8] = {};          // coefficient per window-local bit
   int diag = 0;              // measure diagonal part + norm (output is natural layout)
+  float diag_f[5] = {};      // J, cz bulk / first / last, sum of cz: ep's FP64 values in FP32
   int8_t sigma[16] = {};     // output tile bit of input tile bit q
   // tensor-core pass: TMEM lane m holds tile row XOR over set bits i of m
   // of rowvec[i] (an invertible map, chosen against staging bank conflicts)

@@ -101,7 +101,8 @@ struct Diag {
   __device__ __forceinline__ R operator()(uint64_t x) const {
     int flips = __popcll((x ^ (x >> 1)) & zzmask);
     int nb = __popcll(x & bulkmask);
-    R up = cz_bulk * (R)nb + cz_first * (R)(x & 1) + cz_last * (R)((x >> (L - 1)) & 1);
+    // bit tests as selects: a 64-bit integer to float conversion is slow
+    R up = cz_bulk * (R)nb + ((x & 1) ? cz_first : (R)0) + (((x >> (L - 1)) & 1) ? cz_last : (R)0);
     return J * (R)(L - 1 - 2 * flips) + czsum - (R)2 * up;
   }
 };

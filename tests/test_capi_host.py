@@ -173,12 +173,18 @@ def _block_layout(svlib, L, n):
     sig = np.zeros(64 * 13, np.int32)
     rows = np.zeros(64 * 7, np.uint8)
     wf = np.zeros(64, np.int32)
+    xs = np.zeros(64, np.int32)
     c2 = ctypes.c_int(64)
     assert svlib.sv_host_block_layout(L, ctypes.byref(p), n, ctypes.byref(c2),
                                       a.ctypes.data_as(capi._ip), sig.ctypes.data_as(capi._ip),
-                                      rows.ctypes.data, wf.ctypes.data_as(capi._ip)) == 0
+                                      rows.ctypes.data, wf.ctypes.data_as(capi._ip),
+                                      xs.ctypes.data_as(capi._ip)) == 0
     assert c2.value == P
-    return [lo[k] for k in range(P)], a[:P], sig[:13 * P].reshape(P, 13), rows[:7 * P].reshape(P, 7), wf[:P]
+    los = [lo[k] for k in range(P)]
+    # every site's <X> is measured exactly once per period
+    measured = [los[k] + j for k in range(P) for j in range(n) if (xs[k] >> j) & 1]
+    assert sorted(measured) == list(range(L))
+    return los, a[:P], sig[:13 * P].reshape(P, 13), rows[:7 * P].reshape(P, 7), wf[:P]
 
 
 def _site_position(L, n, lo, s):
@@ -219,21 +225,27 @@ def test_block_tile_layout_and_row_map(svlib, L):
             assert len({rmap[m] & 7 for m in range(m0, m0 + 8)}) == 8
 
         def wavefronts(rowmap):
+            # a 64-bit shared store is served per half-warp: each half takes
+            # as many wavefronts as the most lanes on one 8-byte bank slot
             worst = 0
             for q in range(4):
                 for c in (0, 21, 63):
-                    slots = {}
-                    for t in range(32):
-                        y = c | (rowmap[32 * q + t] << n)
-                        yo = sum(((y >> b) & 1) << int(sig[k, b]) for b in range(13))
-                        byte = 8 * yo
-                        byte ^= ((byte >> 7) & 7) << 4
-                        slots.setdefault((byte >> 3) & 15, set()).add(byte)
-                    worst = max(worst, max(len(v) for v in slots.values()))
+                    total = 0
+                    for half in range(2):
+                        slots = {}
+                        for t in range(16 * half, 16 * half + 16):
+                            y = c | (rowmap[32 * q + t] << n)
+                            yo = sum(((y >> b) & 1) << int(sig[k, b]) for b in range(13))
+                            byte = 8 * yo
+                            byte ^= ((byte >> 7) & 7) << 4
+                            slots.setdefault((byte >> 3) & 15, set()).add(byte)
+                        total += max(len(v) for v in slots.values())
+                    worst = max(worst, total)
             return worst
         got = wavefronts(rmap)
         assert got == wf[k], (k, got, wf[k])
         assert got <= wavefronts(list(range(128)))
     if L == 30:
-        # the two relabels that scattered rows across the banks are fixed
-        assert wf[4] == 4 and wf[5] == 2
+        # relabels that scattered rows across the banks (natural order: 16,
+        # 16, 4, 4 wavefronts) are spread by the row map
+        assert wf[4] == 4 and wf[5] == 2 and wf[11] == 2 and wf[12] == 2

@@ -21,7 +21,9 @@
  *   - the energy  <psi| H0 |psi>,  H0 = sum_b h_b  (Eq. 7, Eq. 10), by
  *     applying every h_b to its four-amplitude groups;
  *   - the reverse-mode gradient of the final energy with respect to
- *     per-period kick angles and transverse fields (adjoint sweep).
+ *     per-period kick angles and transverse fields (adjoint sweep);
+ *   - the energy moments <psi|H0|psi> and <psi|H0^2|psi> = |H0 psi|^2 behind
+ *     E and sigma_E (Eq. 10, Eq. 11), with H0 psi built term by term.
  *
  * Local two-site index: r = 2*b_i + b_{i+1}; site i is the high bit of r,
  * as in the contraction U_{b7 b8 alpha beta} of Eq. 2.
@@ -474,5 +476,36 @@ int or_adjoint(int L, double *psi, int64_t P, const double *hdrive,
     or_period(L, psi, gates, kk, K, first_layer);
   }
   free(lam); free(tmp); free(gates); free(dgates);
+  return OR_OK;
+}
+
+/* ----------------------------------------------------------- energy moments */
+
+/*
+ * e1 = <psi|H0|psi>, e2 = <psi|H0^2|psi> = |H0 psi|^2 and norm2 = <psi|psi>
+ * (unnormalised psi), H0 = sum_b h_b (Eq. 7).  H0 psi is accumulated one
+ * bond term at a time, each applied to a copy of psi by index pairing, so
+ * that sigma_E = sqrt(e2/norm2 - (e1/norm2)^2) follows Eq. 11 directly.
+ */
+int or_energy_moments(int L, const double *psi, const double *hbond, double *e1, double *e2,
+                      double *norm2) {
+  if (L < 2 || !psi || !hbond) return OR_EINVAL;
+  const uint64_t n = 2ull << L;
+  double *hpsi = (double *)calloc(n, sizeof(double));
+  double *tmp = (double *)malloc(n * sizeof(double));
+  if (!hpsi || !tmp) {
+    free(hpsi);
+    free(tmp);
+    return OR_ENOMEM;
+  }
+  for (int b = 0; b < L - 1; ++b) {
+    apply_2q_copy(L, psi, b, hbond + 32 * b, tmp);
+    for (uint64_t k = 0; k < n; ++k) hpsi[k] += tmp[k];
+  }
+  if (e1) *e1 = inner_re(L, psi, hpsi);
+  if (e2) *e2 = inner_re(L, hpsi, hpsi);
+  if (norm2) or_norm2(L, psi, norm2);
+  free(hpsi);
+  free(tmp);
   return OR_OK;
 }

@@ -87,6 +87,11 @@ typedef struct sv_floquet_params {
   int64_t n_period_params;  /* > 0: theta_p / hx_p give one value per period */
   const double *theta_p;    /* host, length n_period_params, or NULL */
   const double *hx_p;       /* host, length n_period_params, or NULL */
+  int32_t inverse;          /* 1: every period applies U_F^dagger instead of U_F (the
+                               kick undone first, then the gates in reverse order,
+                               each replaced by its adjoint), as in the echo of
+                               Sec. V; energies are measured at the end of each
+                               inverse period.  Needs n_period_params = 0. */
 } sv_floquet_params;
 
 /* Library version (an integer that grows with the ABI). */
@@ -156,6 +161,29 @@ int sv_evolve_profiled(sv_ctx *ctx, int64_t periods, double *energy_out,
  * state (host outputs; either may be NULL).  Errors: SV_ESTATE, SV_ECUDA.
  */
 int sv_expect_energy(sv_ctx *ctx, double *energy_density, double *norm2);
+
+/*
+ * Energy moments of the current state (Sec. III.B): energy = E = <H0> and
+ * sigma_e = sqrt(<H0^2> - E^2) of the normalised state (Eq. 10, Eq. 11; the
+ * energy itself, not per site), and norm2 = <psi|psi>; any output may be
+ * NULL.  <H0^2> = |H0 psi|^2 is accumulated with H0 psi formed amplitude by
+ * amplitude from each amplitude's L bit-flip neighbours: no second state is
+ * held, and the state is read about L + 1 times.  Errors: SV_ESTATE,
+ * SV_ECUDA.
+ */
+int sv_energy_moments(sv_ctx *ctx, double *energy, double *sigma_e, double *norm2);
+
+/*
+ * Overlap <phi|psi> of the current state with the product state phi of
+ * `spinors` (host, L*4 doubles as for sv_init; each site's spinor is
+ * normalised): with phi the state sv_init started from, after P periods
+ * and P inverse periods (sv_floquet_params.inverse) this is the echo
+ * overlap of Sec. V, whose error is |1 - <psi(0)|psi'(0)>|.  Computed in FP64
+ * from a table of the low sites times a table of the others.  Errors:
+ * SV_EINVAL, SV_ESTATE, SV_ECUDA.
+ */
+int sv_overlap_product(sv_ctx *ctx, const double *spinors, double *overlap_re,
+                       double *overlap_im);
 
 /* Scale psi to unit norm (FP64 norm); *norm2_before (nullable) gets the
  * squared norm it had.  Errors: SV_ESTATE, SV_ECUDA. */

@@ -13,6 +13,13 @@ The infidelity is computed on the device in FP64. This mirrors the paper's
 accuracy study of long f32 runs against a reference (Sec. V).
 
     python -m paper_2111_08044_gb300.accuracy --L 26 --periods 1000 --every 100
+
+The echo mode follows the paper's own accuracy check (Sec. V) instead: from
+the product state, P periods forward and P inverse periods back in one form,
+then the overlap error |1 - <psi(0)|psi'(0)>| and the relative changes of E
+and sigma_E (Eq. 10-11) between psi(0) and psi'(0):
+
+    python -m paper_2111_08044_gb300.accuracy --echo --L 26 --periods 10,100,1000
 """
 from __future__ import annotations
 
@@ -70,15 +77,49 @@ def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
     return rows
 
 
+def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64"):
+    """The echo of Sec. V for each P in `periods`: P periods forward and P
+    inverse periods back from the product state.  Returns, per P, the
+    overlap error |1 - <psi(0)|psi'(0)>| and the relative changes of E and
+    sigma_E of psi'(0) against psi(0)."""
+    cfg = inputs.ChainConfig(L=L, seed=seed)
+    sp = cfg.spinors()
+    kw = FORMS[form] if precision == "c64" else {}
+    rows = []
+    for P in periods:
+        with FloquetSimulator(L, precision=precision) as sim:
+            sim.init_product_state(sp)
+            sim.build(**chain_params(cfg, **kw))
+            E0, s0, _ = sim.energy_moments()
+            sim.evolve(P, record=False)
+            sim.build(**chain_params(cfg, inverse=1, **kw))
+            sim.evolve(P, record=False)
+            ov = sim.overlap_product(sp)
+            E1, s1, n1 = sim.energy_moments()
+        rows.append({"L": L, "form": form if precision == "c64" else precision, "periods": P,
+                     "total_time": 2 * P * cfg.T, "overlap_error": abs(1.0 - ov),
+                     "rel_err_E": abs(E1 - E0) / abs(E0), "rel_err_sigma": abs(s1 - s0) / s0,
+                     "norm_dev": n1 - 1.0})
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L", type=int, default=26)
-    ap.add_argument("--periods", type=int, default=1000)
+    ap.add_argument("--periods", default="1000",
+                    help="periods (study), or a comma list of P (echo)")
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--forms", default="plain,block_tc")
+    ap.add_argument("--echo", action="store_true")
     a = ap.parse_args()
-    for row in study(a.L, a.periods, a.every, a.seed, tuple(a.forms.split(","))):
+    if a.echo:
+        ps = tuple(int(x) for x in a.periods.split(","))
+        for form in a.forms.split(","):
+            for row in echo(a.L, ps, a.seed, form):
+                print(json.dumps(row), flush=True)
+        return
+    for row in study(a.L, int(a.periods), a.every, a.seed, tuple(a.forms.split(","))):
         print(json.dumps(row), flush=True)
 
 

@@ -61,6 +61,7 @@ class sv_floquet_params(ctypes.Structure):
         ("n_period_params", ctypes.c_int64),
         ("theta_p", ctypes.POINTER(ctypes.c_double)),
         ("hx_p", ctypes.POINTER(ctypes.c_double)),
+        ("inverse", ctypes.c_int32),
     ]
 
 
@@ -95,6 +96,8 @@ SIGNATURES = {
     "sv_host_bond_gates": ([_i32, _pp, _dp, _dp], _i32),
     "sv_host_period_gates": ([_i32, _pp, _ip, _ip, _dp], _i32),
     "sv_host_fusion_plan": ([_i32, _pp, _i32, _ip, _ip, _ip, _dp], _i32),
+    "sv_energy_moments": ([_vp, _dp, _dp, _dp], _i32),
+    "sv_overlap_product": ([_vp, _dp, _dp, _dp], _i32),
     "sv_host_block_layout": ([_i32, _pp, _i32, _ip, _ip, _ip, _vp, _ip, _ip], _i32),
     "sv_batch_state_bytes": ([_i32, _ip], _sz),
     "sv_batch_create": ([ctypes.POINTER(_vp), _i32, _i32, _ip, _pp, _dp, _vp, _sz, _i32, _vp],
@@ -146,7 +149,7 @@ def check(rc: int, ctx=None, what: str = ""):
 
 def make_params(J=1.0, hx=0.9, hz=0.4, T=0.5, theta=0.3, edge_field_weight=0.5, K=4,
                 first_layer=0, mode=SV_MODE_PLAIN, block_n=0, split=SV_SPLIT_BF16X3,
-                renorm_every=0, theta_p=None, hx_p=None):
+                renorm_every=0, theta_p=None, hx_p=None, inverse=0):
     """sv_floquet_params plus the arrays it points to (keep both alive)."""
     import numpy as np
     p = sv_floquet_params()
@@ -154,6 +157,7 @@ def make_params(J=1.0, hx=0.9, hz=0.4, T=0.5, theta=0.3, edge_field_weight=0.5, 
     p.edge_field_weight = edge_field_weight
     p.K, p.first_layer, p.mode, p.block_n, p.split = K, first_layer, mode, block_n, split
     p.renorm_every = renorm_every
+    p.inverse = int(inverse)
     keep = []
     n = 0
     for name, arr in (("theta_p", theta_p), ("hx_p", hx_p)):

@@ -2,6 +2,7 @@
 // gates exp(-i tau h_b) (Eq. 5 of arXiv 2111.08044), the kick, and kick
 // folding.  Independent of the test oracle: gates come from a Jacobi
 // eigendecomposition here, from a Taylor series there.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -214,6 +215,9 @@ bool params_valid(int L, const sv_floquet_params &p, std::string *why) {
   if (p.n_period_params < 0) return bad("n_period_params must be >= 0");
   if (p.n_period_params > 0 && !p.theta_p && !p.hx_p)
     return bad("n_period_params > 0 needs theta_p or hx_p");
+  if (p.inverse != 0 && p.inverse != 1) return bad("inverse must be 0 or 1");
+  if (p.inverse && p.n_period_params > 0)
+    return bad("inverse periods need fixed parameters (n_period_params = 0)");
   return true;
 }
 
@@ -258,6 +262,27 @@ std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
     matmul4(F, g.m, g.m);
   }
   out.back().epi |= EPI_DIAG;
+  if (p.inverse) {
+    // U_F^dagger (the echo of Sec. V): the same gates in reverse order, each
+    // replaced by its adjoint (the folded kicks are then undone first).  Each
+    // site's <X> is read at its last gate of the new order, the diagonal part
+    // at the last gate, so every measurement sees the period's final state.
+    std::reverse(out.begin(), out.end());
+    for (Gate2 &g : out) {
+      cd t[16];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) t[4 * r + c] = std::conj(g.m[4 * c + r]);
+      std::memcpy(g.m, t, sizeof(t));
+      g.epi = 0;
+    }
+    std::vector<int> last2(L, -1);
+    for (int g = 0; g < (int)out.size(); ++g) {
+      last2[out[g].bond] = g;
+      last2[out[g].bond + 1] = g;
+    }
+    for (int i = 0; i < L; ++i) out[last2[i]].epi |= out[last2[i]].bond == i ? EPI_X_HI : EPI_X_LO;
+    out.back().epi |= EPI_DIAG;
+  }
   return out;
 }
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
@@ -703,6 +704,108 @@ int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
   if (rc) return rc;
   DeviceGuard dg(ctx->device);
   return measure(ctx, energy_density, norm2);
+}
+
+int sv_energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm2) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  DeviceGuard dg(ctx->device);
+  const int grid = fsv::moments_grid(ctx->cfg);
+  double* d_part = nullptr;
+  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * 3 * grid,
+                          ctx->stream),
+          "moments scratch");
+  fsv::H0Coef h;
+  h.J = ctx->obs.J;
+  for (int i = 0; i < ctx->L; ++i) {
+    h.cx[i] = ctx->obs.cx[i];
+    h.cz[i] = ctx->obs.cz[i];
+  }
+  std::vector<double> part((size_t)3 * grid);
+  cudaError_t e = fsv::launch_h0_moments(ctx->precision, ctx->state, ctx->L, h, d_part,
+                                         ctx->cfg, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(d_part, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "energy moments");
+  double s1 = 0.0, s2 = 0.0, sn = 0.0;  // fixed order
+  for (int b = 0; b < grid; ++b) {
+    s1 += part[3 * b];
+    s2 += part[3 * b + 1];
+    sn += part[3 * b + 2];
+  }
+  if (!(sn > 0.0)) return fail(ctx, SV_ESTATE, "the state has zero norm");
+  const double E = s1 / sn, var = s2 / sn - E * E;
+  if (energy) *energy = E;
+  if (sigma_e) *sigma_e = std::sqrt(std::max(var, 0.0));
+  if (norm2) *norm2 = sn;
+  return SV_OK;
+}
+
+int sv_overlap_product(sv_ctx* ctx, const double* spinors, double* overlap_re,
+                       double* overlap_im) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (!spinors) return fail(ctx, SV_EINVAL, "null spinors");
+  const int L = ctx->L;
+  // each site's spinor normalised, then the product split into FP64 tables
+  // of the low m sites and of the rest
+  std::vector<std::complex<double>> sp(2 * (size_t)L);
+  for (int i = 0; i < L; ++i) {
+    const std::complex<double> a(spinors[4 * i], spinors[4 * i + 1]),
+        b(spinors[4 * i + 2], spinors[4 * i + 3]);
+    const double nr = std::sqrt(std::norm(a) + std::norm(b));
+    if (!(nr > 0.0) || !std::isfinite(nr))
+      return fail(ctx, SV_EINVAL, "spinor of site %d has no finite norm", i);
+    sp[2 * i] = a / nr;
+    sp[2 * i + 1] = b / nr;
+  }
+  const int m = std::min(L, 12);
+  auto table = [&](int first, int count) {
+    std::vector<double> t(2ull << count);
+    for (uint64_t x = 0; x < (1ull << count); ++x) {
+      std::complex<double> v = 1.0;
+      for (int i = 0; i < count; ++i) v *= sp[2 * (first + i) + ((x >> i) & 1)];
+      t[2 * x] = v.real();
+      t[2 * x + 1] = v.imag();
+    }
+    return t;
+  };
+  const std::vector<double> lo = table(0, m), hi = table(m, L - m);
+  DeviceGuard dg(ctx->device);
+  const int grid = fsv::moments_grid(ctx->cfg);
+  const size_t lo_b = sizeof(double) * lo.size(), hi_b = sizeof(double) * hi.size();
+  char* d_buf = nullptr;
+  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), lo_b + hi_b + sizeof(double) * 2 * grid,
+                          ctx->stream),
+          "overlap scratch");
+  double* d_part = reinterpret_cast<double*>(d_buf + lo_b + hi_b);
+  std::vector<double> part((size_t)2 * grid);
+  cudaError_t e = cudaMemcpyAsync(d_buf, lo.data(), lo_b, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_buf + lo_b, hi.data(), hi_b, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = fsv::launch_product_overlap(ctx->precision, ctx->state, L, m, d_buf, d_buf + lo_b,
+                                    d_part, ctx->cfg, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  // the host tables must outlive the copies above
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(d_buf, ctx->stream);
+  if (e == cudaSuccess) e = es;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "product overlap");
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < grid; ++b) {
+    re += part[2 * b];
+    im += part[2 * b + 1];
+  }
+  if (overlap_re) *overlap_re = re;
+  if (overlap_im) *overlap_im = im;
+  return SV_OK;
 }
 
 int sv_renormalize(sv_ctx* ctx, double* norm2_before) {

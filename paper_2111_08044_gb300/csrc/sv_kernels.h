@@ -85,6 +85,15 @@ struct H0Coef {
 
 // Blocks of the adjoint kernels (also the number of partials each writes).
 int adjoint_grid(const LaunchCfg& cfg);
+// Energy moments (3 partials a block: Re <psi|H0 psi>, |H0 psi|^2, |psi|^2)
+// and the overlap <phi|psi> with a product state phi_x = lo[x mod 2^m]
+// hi[x >> m] (2 partials a block); moments_grid blocks each.
+int moments_grid(const LaunchCfg& cfg);
+cudaError_t launch_h0_moments(int precision, const void* psi, int L, const H0Coef& h,
+                              double* partial, const LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_product_overlap(int precision, const void* psi, int L, int m,
+                                   const void* lo, const void* hi, double* partial,
+                                   const LaunchCfg& cfg, cudaStream_t s);
 
 // lambda = (H0 / L) psi; partial[block] = that block's share of
 // Re <psi|lambda>.

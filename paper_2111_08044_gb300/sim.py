@@ -93,6 +93,24 @@ class FloquetSimulator:
                    self._ctx, "sv_expect_energy")
         return e.value, n.value
 
+    def energy_moments(self) -> Tuple[float, float, float]:
+        """(E, sigma_E, |psi|^2) of the current state: E = <H0> and sigma_E =
+        sqrt(<H0^2> - E^2) on the normalised state (Eq. 10, Eq. 11)."""
+        e, s, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        capi.check(self._lib.sv_energy_moments(self._ctx, ctypes.byref(e), ctypes.byref(s),
+                                               ctypes.byref(n)), self._ctx, "sv_energy_moments")
+        return e.value, s.value, n.value
+
+    def overlap_product(self, spinors: np.ndarray) -> complex:
+        """<phi|psi> with the product state phi of `spinors` ((L, 4) as for
+        init_product_state; each site normalised)."""
+        sp = np.ascontiguousarray(spinors, dtype=np.float64)
+        re, im = ctypes.c_double(), ctypes.c_double()
+        capi.check(self._lib.sv_overlap_product(self._ctx, sp.ctypes.data_as(capi._dp),
+                                                ctypes.byref(re), ctypes.byref(im)),
+                   self._ctx, "sv_overlap_product")
+        return complex(re.value, im.value)
+
     def renormalize(self) -> float:
         n = ctypes.c_double()
         capi.check(self._lib.sv_renormalize(self._ctx, ctypes.byref(n)), self._ctx,

@@ -249,3 +249,30 @@ def test_block_tile_layout_and_row_map(svlib, L):
         # relabels that scattered rows across the banks (natural order: 16,
         # 16, 4, 4 wavefronts) are spread by the row map
         assert wf[4] == 4 and wf[5] == 2 and wf[11] == 2 and wf[12] == 2
+
+
+@pytest.mark.parametrize("L,first", [(6, 0), (7, 1)])
+def test_inverse_period_is_the_adjoint(svlib, L, first):
+    """inverse = 1 gives the forward folded gates in reverse order, each
+    replaced by its adjoint, so that one inverse period undoes U_F (the echo
+    of Sec. V), against the dense Floquet operator."""
+    kw = dict(J=0.9, hx=1.1, hz=0.3, T=0.6, K=3, theta=0.27, first_layer=first)
+    bonds, mats = _period_gates(svlib, L, **kw)
+    ibonds, imats = _period_gates(svlib, L, inverse=1, **kw)
+    np.testing.assert_array_equal(ibonds, bonds[::-1])
+    for k in range(len(bonds)):
+        np.testing.assert_allclose(imats[k], mats[-1 - k].conj().T, atol=0, rtol=0)
+    Ui = np.eye(1 << L, dtype=np.complex128)
+    for b, m in zip(ibonds, imats):
+        Ui = dr.two_site_op(L, int(b), m) @ Ui
+    Ud = dr.floquet_dense([dr.ising_bond_dense(L, b, 0.9, 1.1, 0.3, 0.5) for b in range(L - 1)],
+                          L, 0.2, 0.27, 3, first)
+    np.testing.assert_allclose(Ui, Ud.conj().T, atol=1e-12, rtol=0)
+
+
+def test_inverse_flag_checks(svlib):
+    n = ctypes.c_int(0)
+    p, _ = capi.make_params(inverse=2)
+    assert svlib.sv_host_period_gates(6, ctypes.byref(p), ctypes.byref(n), None, None) == capi.SV_EINVAL
+    p, _ = capi.make_params(inverse=1, theta_p=[0.1, 0.2])
+    assert svlib.sv_host_period_gates(6, ctypes.byref(p), ctypes.byref(n), None, None) == capi.SV_EINVAL

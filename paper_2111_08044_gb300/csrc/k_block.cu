@@ -245,6 +245,26 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
       pa.diag_f[2] = (float)pa.ep.cz_first;
       pa.diag_f[3] = (float)pa.ep.cz_last;
       pa.diag_f[4] = (float)(pa.ep.cz_bulk * (L - 2) + pa.ep.cz_first + pa.ep.cz_last);
+      // per window bit: its site in the (natural) output, its field, and
+      // which of its neighbours lie outside the window
+      int site[8];
+      for (int j = 0; j < n; ++j)
+        site[j] = pa.sigma[j] < n ? pa.sigma[j] : pa.a + pa.sigma[j] - n;
+      for (int j = 0; j < n; ++j) {
+        const int g = site[j];
+        const double czg = g == 0 ? pa.ep.cz_first : (g == L - 1 ? pa.ep.cz_last : pa.ep.cz_bulk);
+        int inside = 0;
+        for (int k = 0; k < 2; ++k) {
+          const int nb = k == 0 ? g - 1 : g + 1;
+          pa.diag_nb[j][k] = -1;
+          if (nb < 0 || nb >= L) continue;
+          bool in_window = false;
+          for (int jj = 0; jj < n; ++jj) in_window = in_window || site[jj] == nb;
+          if (in_window) ++inside;
+          else pa.diag_nb[j][k] = (int8_t)nb;
+        }
+        pa.diag_lin0[j] = (float)(-2.0 * (czg + pa.ep.J * inside));
+      }
     }
     if (pa.x_mask || pa.diag) pa.slot = slot++;
     bp->args.push_back(pa);

@@ -620,15 +620,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         dg.zzmask = (1ull << (pa.L - 1)) - 1;
         dg.bulkmask = ((1ull << pa.L) - 1) & ~1ull & ~(1ull << (pa.L - 1));
         const float h0 = dg(x0);
+        // lin_j = -2 (cz + J sum of the neighbours' z at c = 0): the field and
+        // the window neighbours (bit 0 at c = 0) come precomputed per pass;
+        // only the neighbours outside the window are read from x0
         float lin[kN];
 #pragma unroll
         for (int j = 0; j < kN; ++j) {
-          const int g = gcol(j);
-          float nb = 0.f;  // sum of the neighbours' z at c = 0
-          if (g >= 1) nb += ((x0 >> (g - 1)) & 1) ? -1.f : 1.f;
-          if (g <= pa.L - 2) nb += ((x0 >> (g + 1)) & 1) ? -1.f : 1.f;
-          const float czg = g == 0 ? dg.cz_first : (g == pa.L - 1 ? dg.cz_last : dg.cz_bulk);
-          lin[j] = -2.f * (czg + dg.J * nb);
+          float nb = 0.f;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int ps = pa.diag_nb[j][k];
+            if (ps >= 0) nb += ((x0 >> ps) & 1) ? -1.f : 1.f;
+          }
+          lin[j] = fmaf(-2.f * dg.J, nb, pa.diag_lin0[j]);
         }
         // h(x_c) = h0 + L(c) + Q[c] with L(c) = sum_j c_j lin_j.  The row is
         // taken in pairs (c, c + 1) = (2k, 2k + 1), k in Gray-code order, so

@@ -35,6 +35,11 @@ struct PassArgs {
   float cx[8] = {};          // coefficient per window-local bit
   int diag = 0;              // measure diagonal part + norm (output is natural layout)
   float diag_f[5] = {};      // J, cz bulk / first / last, sum of cz: ep's FP64 values in FP32
+  // diagonal pass, window bit j (output site s_j): lin0[j] = -2 (cz(s_j) + J
+  // * number of neighbours of s_j that are window sites, whose bit is 0 at
+  // c = 0); nb[j][k]: the other neighbours' sites (-1: none)
+  float diag_lin0[8] = {};
+  int8_t diag_nb[8][2] = {};
   int8_t sigma[16] = {};     // output tile bit of input tile bit q
   // tensor-core pass: TMEM lane m holds tile row XOR over set bits i of m
   // of rowvec[i] (an invertible map, chosen against staging bank conflicts)

@@ -92,6 +92,18 @@ typedef struct sv_floquet_params {
                                each replaced by its adjoint), as in the echo of
                                Sec. V; energies are measured at the end of each
                                inverse period.  Needs n_period_params = 0. */
+  const double *h_bonds;    /* NULL: the driven Ising chain above.  Otherwise host,
+                               (L-1) x 16 complex (row-major 4x4, local index
+                               r = 2 b_i + b_{i+1}; site i the high bit): the
+                               Hermitian bond terms H_b of a general two-site chain
+                               (the random circuits of Sec. III.A), whose gates are
+                               exp(-i (T/K) H_b) and whose energy observable is
+                               sum_b H_b (Eq. 7); J, hx, hz and edge_field_weight
+                               are then unused.  sv_evolve does not measure such a
+                               chain per period (its energy and norm outputs are
+                               NaN); sv_energy_moments / sv_expect_energy measure
+                               it on demand.  Needs n_period_params = 0 and
+                               renorm_every = 0. */
 } sv_floquet_params;
 
 /* Library version (an integer that grows with the ABI). */
@@ -123,6 +135,22 @@ int sv_attach_state(sv_ctx *ctx, void *dev_ptr, size_t bytes);
  * (L out of range, buffer too small, zero spinor), SV_ESTATE (no buffer).
  */
 int sv_init(sv_ctx *ctx, int L, const double *product_state);
+
+/*
+ * Dimer-product initial state psi = (x)_k phi_k over the site pairs
+ * (2k, 2k+1), k = 0..L/2-1 (L even): the product of two-site ground states
+ * that starts the evolutions of Sec. III.B (Eq. 9).  pair_states: host,
+ * (L/2) x 4 complex = 4L doubles, local index r = 2 b_{2k} + b_{2k+1} (the
+ * lower site the high bit, as for the bond terms); each pair's vector is
+ * normalised.  Resets the period counter like sv_init.  Errors: SV_EINVAL,
+ * SV_ESTATE, SV_ECUDA.
+ */
+int sv_init_pairs(sv_ctx *ctx, int L, const double *pair_states);
+
+/* <phi|psi> with the dimer-product state phi of pair_states (as for
+ * sv_init_pairs); FP64.  Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA. */
+int sv_overlap_pairs(sv_ctx *ctx, const double *pair_states, double *overlap_re,
+                     double *overlap_im);
 
 /*
  * Build the period: FP64 bond gates exp(-i tau h_b) (Eq. 5), kick folding

@@ -62,6 +62,7 @@ class sv_floquet_params(ctypes.Structure):
         ("theta_p", ctypes.POINTER(ctypes.c_double)),
         ("hx_p", ctypes.POINTER(ctypes.c_double)),
         ("inverse", ctypes.c_int32),
+        ("h_bonds", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -98,6 +99,8 @@ SIGNATURES = {
     "sv_host_fusion_plan": ([_i32, _pp, _i32, _ip, _ip, _ip, _dp], _i32),
     "sv_energy_moments": ([_vp, _dp, _dp, _dp], _i32),
     "sv_overlap_product": ([_vp, _dp, _dp, _dp], _i32),
+    "sv_init_pairs": ([_vp, _i32, _dp], _i32),
+    "sv_overlap_pairs": ([_vp, _dp, _dp, _dp], _i32),
     "sv_host_block_layout": ([_i32, _pp, _i32, _ip, _ip, _ip, _vp, _ip, _ip], _i32),
     "sv_batch_state_bytes": ([_i32, _ip], _sz),
     "sv_batch_create": ([ctypes.POINTER(_vp), _i32, _i32, _ip, _pp, _dp, _vp, _sz, _i32, _vp],
@@ -149,7 +152,7 @@ def check(rc: int, ctx=None, what: str = ""):
 
 def make_params(J=1.0, hx=0.9, hz=0.4, T=0.5, theta=0.3, edge_field_weight=0.5, K=4,
                 first_layer=0, mode=SV_MODE_PLAIN, block_n=0, split=SV_SPLIT_BF16X3,
-                renorm_every=0, theta_p=None, hx_p=None, inverse=0):
+                renorm_every=0, theta_p=None, hx_p=None, inverse=0, h_bonds=None):
     """sv_floquet_params plus the arrays it points to (keep both alive)."""
     import numpy as np
     p = sv_floquet_params()
@@ -167,4 +170,8 @@ def make_params(J=1.0, hx=0.9, hz=0.4, T=0.5, theta=0.3, edge_field_weight=0.5, 
             n = a.size
             setattr(p, name, a.ctypes.data_as(_dp))
     p.n_period_params = n
+    if h_bonds is not None:
+        hb = np.ascontiguousarray(h_bonds, dtype=np.complex128)
+        keep.append(hb)
+        p.h_bonds = hb.ctypes.data_as(_dp)
     return p, keep

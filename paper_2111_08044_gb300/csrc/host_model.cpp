@@ -216,6 +216,25 @@ bool params_valid(int L, const sv_floquet_params &p, std::string *why) {
   if (p.n_period_params > 0 && !p.theta_p && !p.hx_p)
     return bad("n_period_params > 0 needs theta_p or hx_p");
   if (p.inverse != 0 && p.inverse != 1) return bad("inverse must be 0 or 1");
+  if (p.h_bonds) {
+    if (p.n_period_params > 0) return bad("h_bonds needs n_period_params = 0");
+    if (p.renorm_every > 0) return bad("h_bonds needs renorm_every = 0");
+    for (int b = 0; b < L - 1; ++b) {
+      const double *m = p.h_bonds + 32 * (size_t)b;
+      double scale = 0.0;
+      for (int k = 0; k < 32; ++k) {
+        if (!std::isfinite(m[k])) return bad("non-finite h_bonds entry");
+        scale = std::max(scale, std::fabs(m[k]));
+      }
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+          const double dre = m[2 * (4 * r + c)] - m[2 * (4 * c + r)];
+          const double dim = m[2 * (4 * r + c) + 1] + m[2 * (4 * c + r) + 1];
+          if (std::fabs(dre) > 1e-12 * (1.0 + scale) || std::fabs(dim) > 1e-12 * (1.0 + scale))
+            return bad("h_bonds entry is not Hermitian");
+        }
+    }
+  }
   if (p.inverse && p.n_period_params > 0)
     return bad("inverse periods need fixed parameters (n_period_params = 0)");
   return true;
@@ -227,7 +246,11 @@ std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
   std::vector<cd> gb((size_t)16 * (L - 1));
   for (int b = 0; b < L - 1; ++b) {
     cd h[16];
-    bond_hamiltonian(L, b, p.J, hx, p.hz, p.edge_field_weight, h);
+    if (p.h_bonds) {
+      for (int k = 0; k < 16; ++k) h[k] = cd(p.h_bonds[32 * b + 2 * k], p.h_bonds[32 * b + 2 * k + 1]);
+    } else {
+      bond_hamiltonian(L, b, p.J, hx, p.hz, p.edge_field_weight, h);
+    }
     expm_herm4(h, tau, &gb[16 * (size_t)b]);
   }
   std::vector<Gate2> out;
@@ -283,6 +306,9 @@ std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
     for (int i = 0; i < L; ++i) out[last2[i]].epi |= out[last2[i]].bond == i ? EPI_X_HI : EPI_X_LO;
     out.back().epi |= EPI_DIAG;
   }
+  // a general two-site chain has no fused per-period measurement
+  if (p.h_bonds)
+    for (Gate2 &g : out) g.epi = 0;
   return out;
 }
 
@@ -343,6 +369,12 @@ std::vector<AdjOp> adjoint_period_ops(int L, const sv_floquet_params &p, double 
 Observable observable(int L, const sv_floquet_params &p) {
   Observable o;
   o.L = L;
+  if (p.h_bonds) {
+    o.general = true;
+    o.h.resize(16 * (size_t)(L - 1));
+    for (size_t k = 0; k < o.h.size(); ++k) o.h[k] = cd(p.h_bonds[2 * k], p.h_bonds[2 * k + 1]);
+    return o;
+  }
   o.J = p.J;
   o.cx.assign(L, 0.0);
   o.cz.assign(L, 0.0);

@@ -226,13 +226,13 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     const std::string why = block_tile_layout(L, n, R, lo, lo_next, &pa.a, pa.sigma);
     if (!why.empty()) return fail(why);
     if (bp->tensor_cores) block_tc_row_map(pa.sigma, pa.rowvec);
-    for (int s : ps.x_sites) {
+    for (int s : obs.general ? std::vector<int>() : ps.x_sites) {
       const int j = s - lo;
       if (j < 0 || j >= n) return fail("measured site outside window");
       pa.x_mask |= 1u << j;
       pa.cx[j] = (float)obs.cx[s];
     }
-    pa.diag = ps.diag ? 1 : 0;
+    pa.diag = ps.diag && !obs.general ? 1 : 0;
     if (pa.diag) {
       if (lo_next != 0) return fail("last pass must hand back the natural layout");
       pa.ep.flags = EPI_DIAG;

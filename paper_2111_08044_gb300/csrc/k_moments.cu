@@ -6,12 +6,17 @@
 //                      amplitude of H0 psi = D psi + sum_i cx_i X_i psi is
 //                      formed on the fly from psi_x and its L bit-flip
 //                      neighbours, so no second state is held;
+//   k_bond_moments     the same for a general two-site chain (arbitrary
+//                      Hermitian bond terms), from the four amplitudes that
+//                      share each bond's quad;
+//   k_factor_state     writes a product of site-group factors (a product or
+//                      dimer-product initial state) from FP64 tables;
 //   k_product_overlap  per-block partials of <phi|psi> for a product state
 //                      phi_x = lo[x mod 2^m] hi[x >> m] (FP64 factor tables):
 //                      the overlap of an echo's return with its start
 //                      (Sec. V).
-// Both read psi in the natural layout (site i = bit i), which the state
-// holds between periods.
+// All of them address psi in the natural layout (site i = bit i), which the
+// state holds between periods.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -109,6 +114,46 @@ __global__ void __launch_bounds__(kThreads) k_h0_moments(const typename CT<R>::C
   block_store_k<3>(out, partial);
 }
 
+// The same moments for a general two-site chain, H0 = sum_b h_b with
+// arbitrary Hermitian 4x4 bond terms (local index r = 2 b_b + b_{b+1}):
+// (H0 psi)_x = sum_b sum_r' h_b[r_b(x), r'] psi_{x with bits (b, b+1) = r'}.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    k_bond_moments(const typename CT<R>::C* __restrict__ psi, int L,
+                   const typename CT<R>::C* __restrict__ hb, double* partial) {
+  using C = typename CT<R>::C;
+  __shared__ C s_h[33 * 16];
+  for (int k = threadIdx.x; k < 16 * (L - 1); k += blockDim.x) s_h[k] = hb[k];
+  __syncthreads();
+  const uint64_t n = 1ull << L;
+  KahanSum<R> e1, e2, nn;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const C v = psi[x];
+    C hv;
+    hv.x = 0;
+    hv.y = 0;
+    for (int b = 0; b < L - 1; ++b) {
+      const uint64_t bi = 1ull << b, bj = 1ull << (b + 1);
+      const int r = 2 * (int)((x >> b) & 1) + (int)((x >> (b + 1)) & 1);
+      const uint64_t base = x & ~(bi | bj);
+      const C* row = s_h + 16 * b + 4 * r;
+#pragma unroll
+      for (int rp = 0; rp < 4; ++rp) {
+        const C u = psi[base | ((rp >> 1) ? bi : 0) | ((rp & 1) ? bj : 0)];
+        const C m = row[rp];
+        hv.x += m.x * u.x - m.y * u.y;
+        hv.y += m.x * u.y + m.y * u.x;
+      }
+    }
+    e1.add(v.x * hv.x + v.y * hv.y);
+    e2.add(hv.x * hv.x + hv.y * hv.y);
+    nn.add(v.x * v.x + v.y * v.y);
+  }
+  double out[3] = {e1.value(), e2.value(), nn.value()};
+  block_store_k<3>(out, partial);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads)
     k_product_overlap(const typename CT<R>::C* __restrict__ psi, int L, int m,
@@ -132,9 +177,41 @@ __global__ void __launch_bounds__(kThreads)
   block_store_k<2>(out, partial);
 }
 
+// psi_x = lo[x mod 2^m] hi[x >> m] in the state's precision: a product of
+// site-group factors (single sites, or the pairs of a dimer product state)
+// from FP64 tables.
+template <typename R>
+__global__ void __launch_bounds__(kThreads)
+    k_factor_state(typename CT<R>::C* __restrict__ psi, int L, int m,
+                   const double2* __restrict__ lo, const double2* __restrict__ hi) {
+  using C = typename CT<R>::C;
+  const uint64_t n = 1ull << L;
+  const uint64_t mask = (1ull << m) - 1;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const double2 a = lo[x & mask], b = hi[x >> m];
+    C v;
+    v.x = (R)(a.x * b.x - a.y * b.y);
+    v.y = (R)(a.x * b.y + a.y * b.x);
+    psi[x] = v;
+  }
+}
+
 }  // namespace
 
 int moments_grid(const LaunchCfg& cfg) { return cfg.num_sms * kBlocksPerSM; }
+
+cudaError_t launch_factor_state(int precision, void* psi, int L, int m, const void* lo,
+                                const void* hi, const LaunchCfg& cfg, cudaStream_t s) {
+  const int grid = moments_grid(cfg);
+  const double2* l2 = static_cast<const double2*>(lo);
+  const double2* h2 = static_cast<const double2*>(hi);
+  if (precision == SV_C128)
+    k_factor_state<double><<<grid, kThreads, 0, s>>>(static_cast<double2*>(psi), L, m, l2, h2);
+  else
+    k_factor_state<float><<<grid, kThreads, 0, s>>>(static_cast<float2*>(psi), L, m, l2, h2);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_h0_moments(int precision, const void* psi, int L, const H0Coef& h,
                               double* partial, const LaunchCfg& cfg, cudaStream_t s) {
@@ -145,6 +222,18 @@ cudaError_t launch_h0_moments(int precision, const void* psi, int L, const H0Coe
   else
     k_h0_moments<float><<<grid, kThreads, 0, s>>>(static_cast<const float2*>(psi), L, h,
                                                   partial);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bond_moments(int precision, const void* psi, int L, const void* hb,
+                                double* partial, const LaunchCfg& cfg, cudaStream_t s) {
+  const int grid = moments_grid(cfg);
+  if (precision == SV_C128)
+    k_bond_moments<double><<<grid, kThreads, 0, s>>>(static_cast<const double2*>(psi), L,
+                                                     static_cast<const double2*>(hb), partial);
+  else
+    k_bond_moments<float><<<grid, kThreads, 0, s>>>(static_cast<const float2*>(psi), L,
+                                                    static_cast<const float2*>(hb), partial);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <new>
 #include <string>
@@ -357,12 +358,151 @@ int read_ring(sv_ctx* ctx, int64_t c0, int64_t count, double* e_out, double* n_o
                             ctx->stream),
             "copy ring");
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  // a general two-site chain is not measured per period
+  const double nan = std::numeric_limits<double>::quiet_NaN();
   for (int64_t k = 0; k < count; ++k) {
-    if (e_out) e_out[k] = buf[2 * k];
-    if (n_out) n_out[k] = buf[2 * k + 1];
+    if (e_out) e_out[k] = ctx->obs.general ? nan : buf[2 * k];
+    if (n_out) n_out[k] = ctx->obs.general ? nan : buf[2 * k + 1];
   }
   if (ctx->block && fsv::block_status(ctx->block, ctx->stream) != 0)
     return fail(ctx, SV_ETIMEOUT, "a tensor-core block pass gave up a bounded wait");
+  return SV_OK;
+}
+
+// E = <H0>, sigma_E and <psi|psi> of the current state (Ising or general
+// two-site chain), partials summed on the host in a fixed order.
+int energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm2) {
+  const int grid = fsv::moments_grid(ctx->cfg);
+  const bool c128 = ctx->precision == SV_C128;
+  const size_t nh = ctx->obs.general ? ctx->obs.h.size() : 0;
+  const size_t hb_bytes = nh * (c128 ? sizeof(double2) : sizeof(float2));
+  char* d_buf = nullptr;
+  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), hb_bytes + sizeof(double) * 3 * grid,
+                          ctx->stream),
+          "moments scratch");
+  double* d_part = reinterpret_cast<double*>(d_buf + hb_bytes);
+  std::vector<double> part((size_t)3 * grid);
+  std::vector<double2> h64;
+  std::vector<float2> h32;
+  cudaError_t e = cudaSuccess;
+  if (ctx->obs.general) {
+    for (const fsv::cd& v : ctx->obs.h) {
+      h64.push_back(make_double2(v.real(), v.imag()));
+      h32.push_back(make_float2((float)v.real(), (float)v.imag()));
+    }
+    e = cudaMemcpyAsync(d_buf, c128 ? (const void*)h64.data() : (const void*)h32.data(), hb_bytes,
+                        cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = fsv::launch_bond_moments(ctx->precision, ctx->state, ctx->L, d_buf, d_part, ctx->cfg,
+                                   ctx->stream);
+  } else {
+    fsv::H0Coef h;
+    h.J = ctx->obs.J;
+    for (int i = 0; i < ctx->L; ++i) {
+      h.cx[i] = ctx->obs.cx[i];
+      h.cz[i] = ctx->obs.cz[i];
+    }
+    e = fsv::launch_h0_moments(ctx->precision, ctx->state, ctx->L, h, d_part, ctx->cfg,
+                               ctx->stream);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  // the host buffers must outlive the copies above
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(d_buf, ctx->stream);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "energy moments");
+  double s1 = 0.0, s2 = 0.0, sn = 0.0;  // fixed order
+  for (int b = 0; b < grid; ++b) {
+    s1 += part[3 * b];
+    s2 += part[3 * b + 1];
+    sn += part[3 * b + 2];
+  }
+  if (!(sn > 0.0)) return fail(ctx, SV_ESTATE, "the state has zero norm");
+  const double E = s1 / sn, var = s2 / sn - E * E;
+  if (energy) *energy = E;
+  if (sigma_e) *sigma_e = std::sqrt(std::max(var, 0.0));
+  if (norm2) *norm2 = sn;
+  return SV_OK;
+}
+
+// FP64 tables of a product of site-group factors (group = 1: spinors, L x 4
+// doubles; group = 2: pair states, L/2 x 8 doubles with local index
+// r = 2 b_{2k} + b_{2k+1}), each factor normalised: lo over the low m sites,
+// hi over the rest.
+int factor_tables(sv_ctx* ctx, int L, int group, const double* factors, int* m_out,
+                  std::vector<double>* lo, std::vector<double>* hi) {
+  const int ng = L / group, width = 1 << group;
+  std::vector<std::complex<double>> f((size_t)ng * width);
+  for (int g = 0; g < ng; ++g) {
+    double n2 = 0.0;
+    for (int r = 0; r < width; ++r) {
+      f[(size_t)g * width + r] = {factors[2 * (g * width + r)], factors[2 * (g * width + r) + 1]};
+      n2 += std::norm(f[(size_t)g * width + r]);
+    }
+    if (!(n2 > 0.0) || !std::isfinite(n2))
+      return fail(ctx, SV_EINVAL, "factor %d has zero or non-finite norm", g);
+    for (int r = 0; r < width; ++r) f[(size_t)g * width + r] /= std::sqrt(n2);
+  }
+  const int m = std::min(L, 12) / group * group;
+  auto table = [&](int first, int count, std::vector<double>* t) {
+    t->assign(2ull << count, 0.0);
+    for (uint64_t x = 0; x < (1ull << count); ++x) {
+      std::complex<double> v = 1.0;
+      for (int s = 0; s < count; s += group) {
+        int r = 0;  // the group's local index, its lowest site the high bit
+        for (int k = 0; k < group; ++k) r = 2 * r + (int)((x >> (s + k)) & 1);
+        v *= f[(size_t)((first + s) / group) * width + r];
+      }
+      (*t)[2 * x] = v.real();
+      (*t)[2 * x + 1] = v.imag();
+    }
+  };
+  table(0, m, lo);
+  table(m, L - m, hi);
+  *m_out = m;
+  return SV_OK;
+}
+
+// <phi|psi> for the product of site-group factors phi (see factor_tables).
+int product_overlap(sv_ctx* ctx, int group, const double* factors, double* overlap_re,
+                    double* overlap_im) {
+  const int L = ctx->L;
+  std::vector<double> lo, hi;
+  int m = 0;
+  int rc = factor_tables(ctx, L, group, factors, &m, &lo, &hi);
+  if (rc) return rc;
+  DeviceGuard dg(ctx->device);
+  const int grid = fsv::moments_grid(ctx->cfg);
+  const size_t lo_b = sizeof(double) * lo.size(), hi_b = sizeof(double) * hi.size();
+  char* d_buf = nullptr;
+  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), lo_b + hi_b + sizeof(double) * 2 * grid,
+                          ctx->stream),
+          "overlap scratch");
+  double* d_part = reinterpret_cast<double*>(d_buf + lo_b + hi_b);
+  std::vector<double> part((size_t)2 * grid);
+  cudaError_t e = cudaMemcpyAsync(d_buf, lo.data(), lo_b, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_buf + lo_b, hi.data(), hi_b, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = fsv::launch_product_overlap(ctx->precision, ctx->state, L, m, d_buf, d_buf + lo_b,
+                                    d_part, ctx->cfg, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  // the host tables must outlive the copies above
+  const cudaError_t es = cudaStreamSynchronize(ctx->stream);
+  cudaFreeAsync(d_buf, ctx->stream);
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "product overlap");
+  double re = 0.0, im = 0.0;  // fixed order
+  for (int b = 0; b < grid; ++b) {
+    re += part[2 * b];
+    im += part[2 * b + 1];
+  }
+  if (overlap_re) *overlap_re = re;
+  if (overlap_im) *overlap_im = im;
   return SV_OK;
 }
 
@@ -703,6 +843,12 @@ int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   DeviceGuard dg(ctx->device);
+  if (ctx->obs.general) {
+    double E = 0.0;
+    rc = energy_moments(ctx, &E, nullptr, norm2);
+    if (rc == SV_OK && energy_density) *energy_density = E / ctx->L;
+    return rc;
+  }
   return measure(ctx, energy_density, norm2);
 }
 
@@ -710,38 +856,7 @@ int sv_energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   DeviceGuard dg(ctx->device);
-  const int grid = fsv::moments_grid(ctx->cfg);
-  double* d_part = nullptr;
-  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * 3 * grid,
-                          ctx->stream),
-          "moments scratch");
-  fsv::H0Coef h;
-  h.J = ctx->obs.J;
-  for (int i = 0; i < ctx->L; ++i) {
-    h.cx[i] = ctx->obs.cx[i];
-    h.cz[i] = ctx->obs.cz[i];
-  }
-  std::vector<double> part((size_t)3 * grid);
-  cudaError_t e = fsv::launch_h0_moments(ctx->precision, ctx->state, ctx->L, h, d_part,
-                                         ctx->cfg, ctx->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
-                        cudaMemcpyDeviceToHost, ctx->stream);
-  cudaFreeAsync(d_part, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "energy moments");
-  double s1 = 0.0, s2 = 0.0, sn = 0.0;  // fixed order
-  for (int b = 0; b < grid; ++b) {
-    s1 += part[3 * b];
-    s2 += part[3 * b + 1];
-    sn += part[3 * b + 2];
-  }
-  if (!(sn > 0.0)) return fail(ctx, SV_ESTATE, "the state has zero norm");
-  const double E = s1 / sn, var = s2 / sn - E * E;
-  if (energy) *energy = E;
-  if (sigma_e) *sigma_e = std::sqrt(std::max(var, 0.0));
-  if (norm2) *norm2 = sn;
-  return SV_OK;
+  return energy_moments(ctx, energy, sigma_e, norm2);
 }
 
 int sv_overlap_product(sv_ctx* ctx, const double* spinors, double* overlap_re,
@@ -749,62 +864,55 @@ int sv_overlap_product(sv_ctx* ctx, const double* spinors, double* overlap_re,
   int rc = check_ready(ctx, false);
   if (rc) return rc;
   if (!spinors) return fail(ctx, SV_EINVAL, "null spinors");
-  const int L = ctx->L;
-  // each site's spinor normalised, then the product split into FP64 tables
-  // of the low m sites and of the rest
-  std::vector<std::complex<double>> sp(2 * (size_t)L);
-  for (int i = 0; i < L; ++i) {
-    const std::complex<double> a(spinors[4 * i], spinors[4 * i + 1]),
-        b(spinors[4 * i + 2], spinors[4 * i + 3]);
-    const double nr = std::sqrt(std::norm(a) + std::norm(b));
-    if (!(nr > 0.0) || !std::isfinite(nr))
-      return fail(ctx, SV_EINVAL, "spinor of site %d has no finite norm", i);
-    sp[2 * i] = a / nr;
-    sp[2 * i + 1] = b / nr;
-  }
-  const int m = std::min(L, 12);
-  auto table = [&](int first, int count) {
-    std::vector<double> t(2ull << count);
-    for (uint64_t x = 0; x < (1ull << count); ++x) {
-      std::complex<double> v = 1.0;
-      for (int i = 0; i < count; ++i) v *= sp[2 * (first + i) + ((x >> i) & 1)];
-      t[2 * x] = v.real();
-      t[2 * x + 1] = v.imag();
-    }
-    return t;
-  };
-  const std::vector<double> lo = table(0, m), hi = table(m, L - m);
+  return product_overlap(ctx, 1, spinors, overlap_re, overlap_im);
+}
+
+int sv_overlap_pairs(sv_ctx* ctx, const double* pair_states, double* overlap_re,
+                     double* overlap_im) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (!pair_states) return fail(ctx, SV_EINVAL, "null pair_states");
+  if (ctx->L % 2) return fail(ctx, SV_EINVAL, "pair states need an even L");
+  return product_overlap(ctx, 2, pair_states, overlap_re, overlap_im);
+}
+
+int sv_init_pairs(sv_ctx* ctx, int L, const double* pair_states) {
+  if (!ctx) return SV_EINVAL;
+  if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
+  const int lmax = ctx->precision == SV_C128 ? 33 : 34;
+  if (L < 2 || L > lmax || L % 2)
+    return fail(ctx, SV_EINVAL, "L=%d must be even and in 2..%d", L, lmax);
+  if (!pair_states) return fail(ctx, SV_EINVAL, "null pair_states");
+  if (ctx->state_bytes < (amp_bytes(ctx->precision) << L))
+    return fail(ctx, SV_EINVAL, "state buffer of %zu bytes is too small for L=%d",
+                ctx->state_bytes, L);
+  std::vector<double> lo, hi;
+  int m = 0;
+  const int rt = factor_tables(ctx, L, 2, pair_states, &m, &lo, &hi);
+  if (rt) return rt;
   DeviceGuard dg(ctx->device);
-  const int grid = fsv::moments_grid(ctx->cfg);
+  if (L != ctx->L) free_build(ctx);
   const size_t lo_b = sizeof(double) * lo.size(), hi_b = sizeof(double) * hi.size();
   char* d_buf = nullptr;
-  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), lo_b + hi_b + sizeof(double) * 2 * grid,
-                          ctx->stream),
-          "overlap scratch");
-  double* d_part = reinterpret_cast<double*>(d_buf + lo_b + hi_b);
-  std::vector<double> part((size_t)2 * grid);
+  SV_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_buf), lo_b + hi_b, ctx->stream),
+          "pair tables");
   cudaError_t e = cudaMemcpyAsync(d_buf, lo.data(), lo_b, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_buf + lo_b, hi.data(), hi_b, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
-    e = fsv::launch_product_overlap(ctx->precision, ctx->state, L, m, d_buf, d_buf + lo_b,
-                                    d_part, ctx->cfg, ctx->stream);
+    e = fsv::launch_factor_state(ctx->precision, ctx->state, L, m, d_buf, d_buf + lo_b, ctx->cfg,
+                                 ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(part.data(), d_part, sizeof(double) * part.size(),
-                        cudaMemcpyDeviceToHost, ctx->stream);
+    e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(long long), ctx->stream);
   // the host tables must outlive the copies above
   const cudaError_t es = cudaStreamSynchronize(ctx->stream);
   cudaFreeAsync(d_buf, ctx->stream);
   if (e == cudaSuccess) e = es;
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "product overlap");
-  double re = 0.0, im = 0.0;
-  for (int b = 0; b < grid; ++b) {
-    re += part[2 * b];
-    im += part[2 * b + 1];
-  }
-  if (overlap_re) *overlap_re = re;
-  if (overlap_im) *overlap_im = im;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "pair state");
+  ctx->L = L;
+  ctx->inited = true;
+  ctx->counter = 0;
   return SV_OK;
 }
 

@@ -420,6 +420,7 @@ int sv_batch_create(sv_batch** out, int device, int n_chains, const int* L,
   for (int c = 0; c < n_chains; ++c) {
     if (!fsv::params_valid(L[c], params[c], nullptr)) return SV_EINVAL;
     if (params[c].n_period_params != 0) return SV_EINVAL;
+    if (params[c].h_bonds || params[c].inverse) return SV_EUNSUPPORTED;
   }
   sv_batch* b = new (std::nothrow) sv_batch();
   if (!b) return SV_ENOMEM;

@@ -51,6 +51,10 @@ struct Observable {
   int L = 0;
   double J = 0.0;
   std::vector<double> cx, cz;
+  // general two-site chain: H0 = sum_b h[b] (16 complex each); the Ising
+  // fields above are then unused
+  bool general = false;
+  std::vector<cd> h;
 };
 
 // a1: bond Hamiltonian h_b (4x4, r = 2 b_i + b_{i+1}) of the driven chain

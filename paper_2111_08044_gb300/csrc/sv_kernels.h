@@ -91,6 +91,13 @@ int adjoint_grid(const LaunchCfg& cfg);
 int moments_grid(const LaunchCfg& cfg);
 cudaError_t launch_h0_moments(int precision, const void* psi, int L, const H0Coef& h,
                               double* partial, const LaunchCfg& cfg, cudaStream_t s);
+// General two-site chain: hb = (L-1) x 16 complex bond terms on the device
+// (float2 for C64, double2 for C128); same partials as launch_h0_moments.
+cudaError_t launch_bond_moments(int precision, const void* psi, int L, const void* hb,
+                                double* partial, const LaunchCfg& cfg, cudaStream_t s);
+// psi_x = lo[x mod 2^m] hi[x >> m] (lo, hi: FP64 complex tables on the device).
+cudaError_t launch_factor_state(int precision, void* psi, int L, int m, const void* lo,
+                                const void* hi, const LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_product_overlap(int precision, const void* psi, int L, int m,
                                    const void* lo, const void* hi, double* partial,
                                    const LaunchCfg& cfg, cudaStream_t s);

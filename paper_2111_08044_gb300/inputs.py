@@ -150,3 +150,79 @@ def batch_preset(n_chains: int = 512, seed: int = 2, Lmin: int = 14,
     for c in range(n_chains):
         chains[c] = replace(chains[c], seed=rng.next_u64())
     return chains
+
+
+# ------------------------------------------------- the paper's random circuit
+
+def _normal_pair(rng: SplitMix64):
+    """Two independent standard normals from two uniforms (Box and Muller,
+    Ann. Math. Statist. 29 (1958) 610)."""
+    u1 = 1.0 - rng.uniform()  # (0, 1]
+    u2 = rng.uniform()
+    r = math.sqrt(-2.0 * math.log(u1))
+    return r * math.cos(2.0 * math.pi * u2), r * math.sin(2.0 * math.pi * u2)
+
+
+def gue_bond_terms(n_bonds: int, seed: int, frobenius: float = math.sqrt(2.0)) -> np.ndarray:
+    """(n_bonds, 4, 4) complex128 two-site Hamiltonians of the random Floquet
+    circuit of Sec. III.A: each a Gaussian-unitary-ensemble sample
+    (G + G^dagger) / 2, G with independent complex normal entries, shifted
+    to zero trace and scaled to Frobenius norm J = sqrt(2).  Drawn one bond
+    after another (entries row by row, each as (re, im)), so the first L - 1
+    terms are the same for every L, as the paper uses one long list.  The
+    paper's own sample is not available; this is a seeded stand-in."""
+    rng = SplitMix64(seed)
+    out = np.empty((n_bonds, 4, 4), dtype=np.complex128)
+    for b in range(n_bonds):
+        g = np.empty((4, 4), dtype=np.complex128)
+        for r in range(4):
+            for c in range(4):
+                re, im = _normal_pair(rng)
+                g[r, c] = complex(re, im)
+        h = (g + g.conj().T) / 2
+        h = h - (np.trace(h).real / 4) * np.eye(4)
+        out[b] = h * (frobenius / np.linalg.norm(h))
+    return out
+
+
+def pair_ground_states(h_bonds: np.ndarray, L: int) -> np.ndarray:
+    """(L/2, 4): the ground state of each bond term on the site pairs (0, 1),
+    (2, 3), ... (the paper's 1-based odd bonds), the dimer-product initial
+    state of Eq. 9; local index r = 2 b_2k + b_2k+1 as for the bond terms.
+    Each vector's largest entry is made real and positive.  (A 4 x 4
+    eigensolver prepares the input here; neither the oracle nor the library
+    sees anything but the resulting vectors.)"""
+    assert L % 2 == 0 and h_bonds.shape[0] >= L - 1
+    out = np.empty((L // 2, 4), dtype=np.complex128)
+    for k in range(L // 2):
+        w, v = np.linalg.eigh(h_bonds[2 * k])
+        g = v[:, 0]
+        j = int(np.argmax(np.abs(g)))
+        out[k] = g * (abs(g[j]) / g[j])
+    return out
+
+
+@dataclass
+class CircuitConfig:
+    """The paper's random Floquet circuit (Sec. III): L qubits, GUE bond
+    terms H_k, gates exp(-i H_k T), the layer of the paper's even bonds
+    (0-based odd bonds) first, no kick, drive frequency omega = 2 pi / T,
+    started from the dimer-product state of Eq. 9."""
+    L: int
+    omega: float = 6.0
+    seed: int = 11
+
+    @property
+    def T(self) -> float:
+        return 2.0 * math.pi / self.omega
+
+    def h_bonds(self) -> np.ndarray:
+        return gue_bond_terms(self.L - 1, self.seed)
+
+    def pair_states(self) -> np.ndarray:
+        return pair_ground_states(self.h_bonds(), self.L)
+
+    def build_kwargs(self) -> dict:
+        """Keyword arguments of FloquetSimulator.build (plain form; add
+        mode / block_n / split for the block form)."""
+        return dict(h_bonds=self.h_bonds(), T=self.T, K=1, first_layer=1, theta=0.0)

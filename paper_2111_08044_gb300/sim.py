@@ -111,6 +111,23 @@ class FloquetSimulator:
                    self._ctx, "sv_overlap_product")
         return complex(re.value, im.value)
 
+    def init_pairs(self, pair_states: np.ndarray):
+        """Dimer-product initial state over the site pairs (2k, 2k+1):
+        pair_states is (L/2, 4) complex, local index r = 2 b_2k + b_2k+1."""
+        ps = np.ascontiguousarray(pair_states, dtype=np.complex128)
+        assert ps.shape == (self.L // 2, 4)
+        capi.check(self._lib.sv_init_pairs(self._ctx, self.L, ps.ctypes.data_as(capi._dp)),
+                   self._ctx, "sv_init_pairs")
+
+    def overlap_pairs(self, pair_states: np.ndarray) -> complex:
+        """<phi|psi> with the dimer-product state of pair_states."""
+        ps = np.ascontiguousarray(pair_states, dtype=np.complex128)
+        re, im = ctypes.c_double(), ctypes.c_double()
+        capi.check(self._lib.sv_overlap_pairs(self._ctx, ps.ctypes.data_as(capi._dp),
+                                              ctypes.byref(re), ctypes.byref(im)),
+                   self._ctx, "sv_overlap_pairs")
+        return complex(re.value, im.value)
+
     def renormalize(self) -> float:
         n = ctypes.c_double()
         capi.check(self._lib.sv_renormalize(self._ctx, ctypes.byref(n)), self._ctx,

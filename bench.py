@@ -127,9 +127,15 @@ def _max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _rank_seed(rank):
+    """Seed of this replica's product state: each rank evolves its own chain."""
+    return 4 + rank
 
 
 def _time_form(args, mode, steps, rank, world, local):
@@ -141,7 +147,7 @@ def _time_form(args, mode, steps, rank, world, local):
     from paper_2111_08044_gb300 import capi, inputs
     from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
 
-    cfg = inputs.ChainConfig(L=args.L, seed=4 + rank)
+    cfg = inputs.ChainConfig(L=args.L, seed=_rank_seed(rank))
     split = capi.SV_SPLIT_BF16X3 if args.split == "bf16x3" else capi.SV_SPLIT_FP32
     kw = chain_params(cfg)
     if mode == "block":
@@ -191,7 +197,7 @@ def _e2e(args, steps, rank, local):
     from paper_2111_08044_gb300 import capi, inputs
     from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
 
-    cfg = inputs.ChainConfig(L=args.L, seed=4 + rank)
+    cfg = inputs.ChainConfig(L=args.L, seed=_rank_seed(rank))
     kw = chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=args.n,
                       split=capi.SV_SPLIT_BF16X3 if args.split == "bf16x3" else capi.SV_SPLIT_FP32)
     sim = FloquetSimulator(cfg.L, device=local)

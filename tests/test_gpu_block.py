@@ -83,3 +83,19 @@ def test_tensor_core_100_periods_with_renormalisation(svlib, L):
     np.testing.assert_allclose(e, e_o, atol=1e-5, rtol=0)
     assert np.all(np.abs(nn - 1.0) < 2e-5)  # one period of drift at most
     assert _infidelity(psi, psi_o) < 1e-5
+
+
+@pytest.mark.parametrize("L,first,ew,periods", [(15, 1, 1.0, 3), (21, 0, 1.0, 2), (26, 1, 0.5, 1)])
+def test_tensor_core_variants_match_oracle(svlib, L, first, ew, periods):
+    """Odd L, the other layer order and whole edge fields; at L = 26 the CTAs
+    run 54 tiles each (a ragged tail over 152 SMs), so the pass instances
+    specialised on what they measure are checked element by element."""
+    cfg = inputs.ChainConfig(L=L, periods=periods, seed=90 + L, first_layer=first,
+                             edge_field_weight=ew)
+    psi_o, _, e_o, n_o = orc.run_chain(cfg)
+    e, nn, psi, info = _run_block(cfg, 6, capi.SV_SPLIT_BF16X3, cfg.periods, expect_tc=True)
+    assert _infidelity(psi, psi_o) < 1e-8
+    err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
+    assert err < 4e-6 * np.sqrt(cfg.periods * info[0]), err
+    np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(nn, n_o, atol=5e-6, rtol=0)

@@ -4,7 +4,8 @@
 // paper's fused >= 7-qubit operators (Sec. II: contractions on index
 // groups of 2^7 to fit the matrix unit).
 //
-// Search: beam search over (gates done, current window).  A pass may take
+// Search: beam search over (gates done, current window), its levels
+// expanded on the host's cores and its result cached per gate structure.  A pass may take
 // every pending gate inside its window whose predecessors are done.  Moving
 // the window by more than 7 sites costs extra relabel-only passes (the
 // state layout changes through a 7-bit row index), as does returning to the
@@ -12,6 +13,9 @@
 // starts from the natural layout.
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <unordered_set>
 
 #include "sv_internal.h"
@@ -25,10 +29,12 @@ constexpr int kMaxShift = 7;
 struct Dag {
   std::vector<int> bond;
   std::vector<std::vector<int>> pred;
+  std::vector<std::vector<int>> by_bond;  // gate indices per bond, in order
 };
 
 Dag make_dag(const std::vector<Gate2>& gates, int L) {
   Dag d;
+  d.by_bond.resize(L);
   std::vector<int> last(L, -1);
   for (size_t k = 0; k < gates.size(); ++k) {
     const int b = gates[k].bond;
@@ -37,6 +43,7 @@ Dag make_dag(const std::vector<Gate2>& gates, int L) {
     if (last[b] >= 0) p.push_back(last[b]);
     if (last[b + 1] >= 0 && last[b + 1] != last[b]) p.push_back(last[b + 1]);
     d.pred.push_back(p);
+    d.by_bond[b].push_back((int)k);
     last[b] = last[b + 1] = (int)k;
   }
   return d;
@@ -46,18 +53,26 @@ struct State {
   std::vector<uint64_t> done;
   int count = 0;
   int lo = -1;
-  std::vector<std::pair<int, std::vector<int>>> hist;  // (lo, gates)
+  // the pass that led here: its gates, the relabel-only passes before it,
+  // and the state it came from (level, index among that level's kept states)
+  std::vector<int> ab;
+  int relabels = 0;
+  int plevel = -1, pindex = -1;
 };
 
 inline bool test(const std::vector<uint64_t>& s, int k) { return (s[k >> 6] >> (k & 63)) & 1; }
 inline void set(std::vector<uint64_t>& s, int k) { s[k >> 6] |= 1ull << (k & 63); }
 
 std::vector<int> absorb(const Dag& d, std::vector<uint64_t>& done, int lo, int n) {
+  // the pending gates on the window's bonds, in the period's order (a gate
+  // taken here can ready a later one in the same window)
+  std::vector<int> cand;
+  for (int b = lo; b + 1 < lo + n && b < (int)d.by_bond.size(); ++b)
+    for (int k : d.by_bond[b])
+      if (!test(done, k)) cand.push_back(k);
+  std::sort(cand.begin(), cand.end());
   std::vector<int> ab;
-  for (size_t k = 0; k < d.bond.size(); ++k) {
-    if (test(done, (int)k)) continue;
-    const int b = d.bond[k];
-    if (b < lo || b + 1 >= lo + n) continue;
+  for (int k : cand) {
     bool ready = true;
     for (int p : d.pred[k])
       if (!test(done, p)) {
@@ -85,18 +100,32 @@ size_t key_hash(const State& s) {
 
 }  // namespace
 
-std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n) {
-  const Dag dag = make_dag(gates, L);
-  const int ng = (int)gates.size();
+namespace {
+
+using Hist = std::vector<std::pair<int, std::vector<int>>>;  // (lo or -1, gates) per pass
+
+// The beam search: the best sequence of windows for the gate DAG.  The kept
+// states of a level are expanded on the host's cores; their candidates are
+// merged in the order a single thread would produce them, so the plan does
+// not depend on the thread count.  States link to their parents; the
+// sequence of passes is read back once at the end.
+Hist plan_search(const Dag& dag, int L, int n, int ng) {
   const int words = (ng + 63) / 64;
   const size_t beam = ng <= 200 ? 256 : 32;
   // levels[k]: states after k passes (relabel-only passes included)
   std::vector<std::vector<State>> levels(1);
+  std::vector<std::vector<State>> archive;  // kept states per level (parents)
   State s0;
   s0.done.assign(words, 0);
   levels[0].push_back(s0);
   int best_total = 1 << 30;
   State best;
+  int best_tail = 0;  // relabel-only passes back to site 0 after the last window
+  struct Cand {
+    State t;
+    int kk;
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
   for (int k = 0; k < (int)levels.size() && k < best_total; ++k) {
     std::vector<State> lv = std::move(levels[k]);
     levels[k].clear();
@@ -105,39 +134,94 @@ std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n
       return a.lo < b.lo;
     });
     std::unordered_set<size_t> seen;
-    std::vector<State> kept;
+    if ((int)archive.size() <= k) archive.resize(k + 1);
+    std::vector<State>& kept = archive[k];
     for (auto& s : lv) {
       if (kept.size() >= beam) break;
       if (seen.insert(key_hash(s)).second) kept.push_back(std::move(s));
     }
-    for (const State& s : kept) {
-      const int lo_max = s.lo < 0 ? 0 : L - n;  // the first window starts at site 0
-      for (int lo = 0; lo <= lo_max; ++lo) {
-        State t;
-        t.done = s.done;
-        std::vector<int> ab = absorb(dag, t.done, lo, n);
-        if (ab.empty()) continue;
-        t.count = s.count + (int)ab.size();
-        t.lo = lo;
-        const int cost = 1 + (s.lo < 0 ? 0 : shift_cost(s.lo, lo));
-        t.hist = s.hist;
-        for (int e = 0; e < cost - 1; ++e) t.hist.push_back({-1, {}});  // relabel-only
-        t.hist.push_back({lo, ab});
-        const int kk = k + cost;
-        if (t.count == ng) {
-          const int total = kk + shift_cost(lo, 0);
+    std::vector<std::vector<Cand>> per(kept.size());
+    auto expand = [&](size_t i0, size_t i1) {
+      for (size_t i = i0; i < i1; ++i) {
+        const State& s = kept[i];
+        const int lo_max = s.lo < 0 ? 0 : L - n;  // the first window starts at site 0
+        for (int lo = 0; lo <= lo_max; ++lo) {
+          State t;
+          t.done = s.done;
+          t.ab = absorb(dag, t.done, lo, n);
+          if (t.ab.empty()) continue;
+          t.count = s.count + (int)t.ab.size();
+          t.lo = lo;
+          const int cost = 1 + (s.lo < 0 ? 0 : shift_cost(s.lo, lo));
+          t.relabels = cost - 1;
+          t.plevel = k;
+          t.pindex = (int)i;
+          per[i].push_back({std::move(t), k + cost});
+        }
+      }
+    };
+    const size_t nt = std::min<size_t>(hw, kept.size() / 4);
+    if (nt <= 1) {
+      expand(0, kept.size());
+    } else {
+      std::vector<std::thread> th;
+      const size_t chunk = (kept.size() + nt - 1) / nt;
+      for (size_t t = 0; t < nt; ++t)
+        th.emplace_back(expand, t * chunk, std::min(kept.size(), (t + 1) * chunk));
+      for (auto& x : th) x.join();
+    }
+    for (auto& cs : per)
+      for (Cand& c : cs) {
+        if (c.t.count == ng) {
+          const int total = c.kk + shift_cost(c.t.lo, 0);
           if (total < best_total) {
             best_total = total;
-            best = t;
-            for (int e = 0; e < shift_cost(lo, 0); ++e) best.hist.push_back({-1, {}});
+            best = c.t;
+            best_tail = shift_cost(c.t.lo, 0);
           }
           continue;
         }
-        if ((int)levels.size() <= kk) levels.resize(kk + 1);
-        levels[kk].push_back(std::move(t));
+        if ((int)levels.size() <= c.kk) levels.resize(c.kk + 1);
+        levels[c.kk].push_back(std::move(c.t));
       }
-    }
   }
+  // read the passes back along the parent links
+  Hist rev;
+  for (int e = 0; e < best_tail; ++e) rev.push_back({-1, {}});
+  const State* st = &best;
+  while (st && st->plevel >= 0) {
+    rev.push_back({st->lo, st->ab});
+    for (int e = 0; e < st->relabels; ++e) rev.push_back({-1, {}});
+    st = &archive[st->plevel][st->pindex];
+  }
+  return Hist(rev.rbegin(), rev.rend());
+}
+
+// Plans depend only on the gate structure (bond sequence, L, n), not on the
+// gate values: a rebuild with new parameters reuses the search.
+Hist cached_plan(const Dag& dag, int L, int n, int ng) {
+  static std::mutex mu;
+  static std::map<std::vector<int>, Hist> cache;
+  std::vector<int> key{L, n};
+  key.insert(key.end(), dag.bond.begin(), dag.bond.end());
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  Hist h = plan_search(dag, L, n, ng);
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() >= 64) cache.clear();
+  cache.emplace(std::move(key), h);
+  return h;
+}
+
+}  // namespace
+
+std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n) {
+  const Dag dag = make_dag(gates, L);
+  const int ng = (int)gates.size();
+  const Hist hist = cached_plan(dag, L, n, ng);
   // Materialise passes: fused unitaries, energy flags.  A relabel-only pass
   // keeps an identity unitary on a window that steps toward the next one.
   std::vector<BlockPass> out;
@@ -148,18 +232,18 @@ std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n
     last_gate[gates[k].bond + 1] = k;
   }
   int prev_lo = 0;
-  for (size_t h = 0; h < best.hist.size(); ++h) {
+  for (size_t h = 0; h < hist.size(); ++h) {
     BlockPass p;
     p.n = n;
-    if (best.hist[h].first >= 0) {
-      p.lo = best.hist[h].first;
-      p.gates = best.hist[h].second;
+    if (hist[h].first >= 0) {
+      p.lo = hist[h].first;
+      p.gates = hist[h].second;
     } else {
       // find the next real window (or site 0 at the end) and step toward it
       int target = 0;
-      for (size_t q = h + 1; q < best.hist.size(); ++q)
-        if (best.hist[q].first >= 0) {
-          target = best.hist[q].first;
+      for (size_t q = h + 1; q < hist.size(); ++q)
+        if (hist[q].first >= 0) {
+          target = hist[q].first;
           break;
         }
       const int step = std::max(-kMaxShift, std::min(kMaxShift, target - prev_lo));

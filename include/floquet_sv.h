@@ -347,12 +347,16 @@ int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
  *                            conflicts; 0 if not a tensor-core pass);
  *   x_sites_out[k]           bit j set if the pass measures <X> of window
  *                            site window_lo + j (each site once per period,
- *                            in the pass holding its last gate).
+ *                            in the pass holding its last gate);
+ *   staging_out[13k + o]     tensor-core pass: the bit of the staging tile
+ *                            that holds output tile bit o (o for the natural
+ *                            order; bits 0-3 always stay in place).
  * Errors: SV_EINVAL.
  */
 int sv_host_block_layout(int L, const sv_floquet_params *p, int n, int *n_passes,
                          int *tile_a, int *sigma_out, unsigned char *rows_out,
-                         int *store_wavefronts, int *x_sites_out);
+                         int *store_wavefronts, int *x_sites_out,
+                         unsigned char *staging_out);
 
 /* ------------------------------------------------------------------ batch
  * Many independent chains (each its own L, parameters and product state)

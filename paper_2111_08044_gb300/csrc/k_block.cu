@@ -225,7 +225,7 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     pa.ntiles = ntiles;
     const std::string why = block_tile_layout(L, n, R, lo, lo_next, &pa.a, pa.sigma);
     if (!why.empty()) return fail(why);
-    if (bp->tensor_cores) block_tc_row_map(pa.sigma, pa.rowvec);
+    if (bp->tensor_cores) block_tc_layout(pa);
     for (int s : obs.general ? std::vector<int>() : ps.x_sites) {
       const int j = s - lo;
       if (j < 0 || j >= n) return fail("measured site outside window");

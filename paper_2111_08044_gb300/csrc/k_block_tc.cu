@@ -184,6 +184,22 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t sr
       "r"(src), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group"
+      " [%0, {%2, %3, %4, %5}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group"
+      " [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(reinterpret_cast<uint64_t>(map)),
+      "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
 // Byte offset of a staging-tile byte under the 128-byte swizzle: the
 // 16-byte chunk index (bits 4-6) is XORed with the 128-byte line index
 // modulo 8 (bits 7-9).  Linear over XOR.
@@ -504,12 +520,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     // contiguous 64 amplitudes), bits 6-12 the next rows.  The staging tile
     // holds amplitude y at byte swz128(8 y), so the place of this row's
     // element c is row_off ^ (XOR over set bits j of c of col_off[j]).
-    uint32_t yrow = 0;
-    for (int bq = 0; bq < 7; ++bq) yrow |= ((uint32_t)(r >> bq) & 1u) << pa.sigma[kN + bq];
-    const uint32_t row_off = swz128(8u * yrow);
+    // Output bit o sits at bit spos[o] of the staging tile (ssig = spos o
+    // sigma), an order chosen per pass against bank conflicts of the stores.
+    uint32_t yrow = 0, ystage = 0;
+    for (int bq = 0; bq < 7; ++bq) {
+      yrow |= ((uint32_t)(r >> bq) & 1u) << pa.sigma[kN + bq];
+      ystage |= ((uint32_t)(r >> bq) & 1u) << pa.ssig[kN + bq];
+    }
+    const uint32_t row_off = swz128(8u * ystage);
     uint32_t col_off[kN];
 #pragma unroll
-    for (int j = 0; j < kN; ++j) col_off[j] = swz128(8u << pa.sigma[j]);
+    for (int j = 0; j < kN; ++j) col_off[j] = swz128(8u << pa.ssig[j]);
     const uint32_t out_base = sbase + kOffOut;
     // Diagonal part on the natural layout (the period's last pass), per
     // amplitude h(x) = J sum_p z_p z_{p+1} + sum_p cz_p z_p, z = 1 - 2 x_p.
@@ -688,7 +709,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       epilogue_sync();
       if (elected) {
-        tma_store_3d(&tmap_out, out_base, 0, (int)(tlo << 2), (int)(thi << 7));
+        if (pa.st_ndims == 3) {
+          // the natural order: output bits 4-5, then the rows
+          tma_store_3d(&tmap_out, out_base, 0, (int)(tlo << 2), (int)(thi << 7));
+        } else {
+          // the tile-index bits go to the store view's dimensions that their
+          // state bits continue
+          auto coord = [&](int d) {
+            return (d == pa.st_tlo_dim ? (int)(tlo << pa.st_tlo_shift) : 0) |
+                   (d == pa.st_thi_dim ? (int)(thi << pa.st_thi_shift) : 0);
+          };
+          if (pa.st_ndims == 4)
+            tma_store_4d(&tmap_out, out_base, 0, coord(1), coord(2), coord(3));
+          else
+            tma_store_5d(&tmap_out, out_base, 0, coord(1), coord(2), coord(3), coord(4));
+        }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
@@ -866,11 +901,11 @@ bool block_tc_supported(int L, int n) { return n == kN && L >= kN + 7; }
 size_t block_tc_w_bytes(int n) { return n == kN ? kWBytes : 0; }
 
 namespace {
-// 8-byte slot (bank pair, 0..15) contributed by output tile bit o to a
+// 8-byte slot (bank pair, 0..15) contributed by staging-tile bit p to a
 // staging byte address under the 128-byte swizzle: amplitude bits 0-3 are
 // slot bits 0-3, bits 4-6 are XORed into slot bits 1-3, and higher bits only
 // select the 128-byte line.
-int staging_slot_bit(int o) { return o < 4 ? 1 << o : (o < 7 ? 1 << (o - 3) : 0); }
+int staging_slot_bit(int p) { return p < 4 ? 1 << p : (p < 7 ? 1 << (p - 3) : 0); }
 // Rank over GF(2) of k bit vectors of at most 8 bits.
 int gf2_rank(const int* v, int k) {
   int piv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -891,14 +926,14 @@ int gf2_rank(const int* v, int k) {
 }
 }  // namespace
 
-int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec) {
+int block_tc_row_map(const int8_t* sigma, const int8_t* spos, uint8_t* rowvec) {
   // The 32 lanes of an epilogue warp are TMEM lanes 32q + t, and a 64-bit
   // shared store is served per half-warp (lanes 0-15, then 16-31).  With
   // rows r(m) = M m over GF(2) the staging slot of lane t's store is linear
   // in t, so each half takes 2^(4 - rank) wavefronts, where rank is that of
   // the slot images of M's first four columns (4 at best: one lane a slot).
   int v[7];
-  for (int b = 0; b < 7; ++b) v[b] = staging_slot_bit(sigma[kN + b]);
+  for (int b = 0; b < 7; ++b) v[b] = staging_slot_bit(spos[sigma[kN + b]]);
   auto img = [&](int m) {
     int x = 0;
     for (int b = 0; b < 7; ++b)
@@ -958,6 +993,125 @@ int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec) {
   return 2 << (4 - best);
 }
 
+namespace {
+// State bit of output tile bit o for a tile whose rows start at state bit a:
+// bits 0-5 are the next window, bits 6-12 the rows.
+int out_state_bit(int o, int a) { return o < kN ? o : a + o - kN; }
+
+// The store view of a staging order: staging bits 0-3 are one 128-byte line
+// (dimension 0), and staging bits 4-12 split into runs of output bits on
+// consecutive state bits, one dimension each (output bit 6 always starts a
+// run: the tile-index bits below the rows lie between bits 5 and 6).
+// Returns the number of runs, with the first output bit and length of each.
+int store_runs(const int8_t* spos, int a, int* first, int* len) {
+  int inv[13];
+  for (int o = 0; o < 13; ++o) inv[spos[o]] = o;
+  int nr = 0;
+  for (int p = 4; p < 13; ++p) {
+    const int o = inv[p];
+    if (p > 4 && o != kN && out_state_bit(o, a) == out_state_bit(inv[p - 1], a) + 1) {
+      ++len[nr - 1];
+    } else {
+      if (nr == 9) return 99;
+      first[nr] = o;
+      len[nr++] = 1;
+    }
+  }
+  return nr;
+}
+
+// Fills the store fields of pa from pa.spos; false if the view needs more
+// than the five dimensions a tensor map has.
+bool set_store_view(PassArgs& pa) {
+  int first[9], len[9];
+  const int nr = store_runs(pa.spos, pa.a, first, len);
+  if (nr > 4) return false;
+  // a three-dimensional view is stored with the natural order's coordinates
+  if (nr == 2 && (first[0] != 4 || len[0] != 2)) return false;
+  pa.st_ndims = (int8_t)(nr + 1);
+  for (int k = 0; k < nr; ++k) {
+    const int last = first[k] + len[k] - 1;
+    if (last == kN - 1) {  // the tile bits below the rows continue this run
+      pa.st_tlo_dim = (int8_t)(k + 1);
+      pa.st_tlo_shift = (int8_t)len[k];
+    }
+    if (last == 12) {  // the tile bits above the rows
+      pa.st_thi_dim = (int8_t)(k + 1);
+      pa.st_thi_shift = (int8_t)len[k];
+    }
+  }
+  for (int q = 0; q < 13; ++q) pa.ssig[q] = pa.spos[pa.sigma[q]];
+  return true;
+}
+
+// Largest rank the row map can give the slot images of its first four
+// columns (columns 0-2 hold row bits 0-2 plus any of rows 3-6): a quick
+// bound used to rank staging orders before the row map is searched.
+int row_map_reach(const int* v) {
+  const int rv = std::min(4, gf2_rank(v, 7));
+  int span[16];
+  for (int c = 0; c < 16; ++c) {
+    span[c] = 0;
+    for (int b = 0; b < 4; ++b)
+      if ((c >> b) & 1) span[c] ^= v[3 + b];
+  }
+  int k = 0;
+  for (int i = 0; i < 16 && k < 3; ++i)
+    for (int j = 0; j < 16 && k < 3; ++j)
+      for (int l = 0; l < 16 && k < 3; ++l) {
+        const int t[3] = {v[0] ^ span[i], v[1] ^ span[j], v[2] ^ span[l]};
+        k = std::max(k, gf2_rank(t, 3));
+      }
+  return std::min(rv, k + 1);
+}
+}  // namespace
+
+// Stores at 8 wavefronts cost less than the scattered writes of a
+// reordered store view; at 16 the conflicts dominate the pass.
+constexpr int kRestageWavefronts = 16;
+
+int block_tc_layout(PassArgs& pa) {
+  for (int o = 0; o < 13; ++o) pa.spos[o] = (int8_t)o;
+  set_store_view(pa);  // the natural order: three dimensions
+  const int wf = block_tc_row_map(pa.sigma, pa.spos, pa.rowvec);
+  if (wf < kRestageWavefronts) return wf;
+  // Output bits for staging bits 4-6 (slot bits 1-3), the others above them
+  // in increasing order; the best reach with the fewest store dimensions.
+  int best_reach = -1, best_runs = 99;
+  int8_t best[13];
+  for (int x = 4; x < 13; ++x)
+    for (int y = 4; y < 13; ++y)
+      for (int z = 4; z < 13; ++z) {
+        if (x == y || x == z || y == z) continue;
+        int8_t sp[13];
+        for (int o = 0; o < 4; ++o) sp[o] = (int8_t)o;
+        sp[x] = 4;
+        sp[y] = 5;
+        sp[z] = 6;
+        int p = 7;
+        for (int o = 4; o < 13; ++o)
+          if (o != x && o != y && o != z) sp[o] = (int8_t)p++;
+        int first[9], len[9];
+        const int nr = store_runs(sp, pa.a, first, len);
+        if (nr > 4) continue;
+        int v[7];
+        for (int b = 0; b < 7; ++b) v[b] = staging_slot_bit(sp[pa.sigma[kN + b]]);
+        const int reach = row_map_reach(v);
+        if (reach > best_reach || (reach == best_reach && nr < best_runs)) {
+          best_reach = reach;
+          best_runs = nr;
+          std::memcpy(best, sp, sizeof(best));
+        }
+      }
+  if (best_reach < 0) return wf;
+  PassArgs t = pa;
+  std::memcpy(t.spos, best, sizeof(best));
+  const int wf2 = block_tc_row_map(t.sigma, t.spos, t.rowvec);
+  if (wf2 >= wf || !set_store_view(t)) return wf;
+  pa = t;
+  return wf2;
+}
+
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
   // six K-major 64 x 64 bf16 digit matrices Ur0, Ur1, Ur2, Ui0, Ui1, Ui2
   // holding u0/128, u1/32768, u2/2^23 with u = 2^-7 (u0 + u1/256 + u2/65536),
@@ -989,9 +1143,10 @@ void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out
 
 // Two descriptors per pass: the load view (tile rows as 128-row boxes of
 // 128 bytes: window amplitudes 16 c .. 16 c + 15 of each row) and the store
-// view (the staging tile's output order: amplitudes 0-15 of an output row,
-// output bits 4-5 joined with the tile bits below the row bits, output row
-// bits 6-12 joined with the tile bits above them).
+// view of the staging order: amplitudes 0-15 of an output row, then one
+// dimension per run of the staging order (natural order: output bits 4-5
+// joined with the tile bits below the row bits, output row bits 6-12 joined
+// with the tile bits above them).
 int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return SV_ECUDA;
@@ -1006,10 +1161,21 @@ int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) return SV_ECUDA;
   // store view: 8-byte elements (one complex amplitude each)
-  cuuint64_t odims[3] = {16, (cuuint64_t)1 << (a - 4), (cuuint64_t)1 << (L - a)};
-  cuuint64_t ostrides[2] = {128, (cuuint64_t)8 << a};
-  cuuint32_t obox[3] = {16, 4, 128};
-  rc = fn(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, psi, odims, ostrides, obox, estr,
+  int first[9], len[9];
+  const int nr = store_runs(pa.spos, a, first, len);
+  if (nr > 4 || nr + 1 != pa.st_ndims) return SV_EINVAL;
+  cuuint64_t odims[5] = {16, 1, 1, 1, 1}, ostrides[4] = {0, 0, 0, 0};
+  cuuint32_t obox[5] = {16, 1, 1, 1, 1};
+  for (int k = 0; k < nr; ++k) {
+    const int last = first[k] + len[k] - 1;
+    int bits = len[k];
+    if (last == kN - 1) bits += a - kN;
+    if (last == 12) bits += L - a - 7;
+    odims[k + 1] = (cuuint64_t)1 << bits;
+    ostrides[k] = (cuuint64_t)8 << out_state_bit(first[k], a);
+    obox[k + 1] = 1u << len[k];
+  }
+  rc = fn(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, nr + 1, psi, odims, ostrides, obox, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) return SV_ECUDA;

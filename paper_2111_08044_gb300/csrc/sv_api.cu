@@ -1222,7 +1222,8 @@ int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
 
 int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes,
                          int* tile_a, int* sigma_out, unsigned char* rows_out,
-                         int* store_wavefronts, int* x_sites_out) {
+                         int* store_wavefronts, int* x_sites_out,
+                         unsigned char* staging_out) {
   if (!p || !n_passes) return SV_EINVAL;
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
   if (n < 2 || n > 7 || n >= L) return SV_EINVAL;
@@ -1231,7 +1232,8 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
   const int P = (int)plan.size();
   const int cap = *n_passes;
   *n_passes = P;
-  if (!tile_a && !sigma_out && !rows_out && !store_wavefronts && !x_sites_out) return SV_OK;
+  if (!tile_a && !sigma_out && !rows_out && !store_wavefronts && !x_sites_out && !staging_out)
+    return SV_OK;
   if (cap < P) return SV_EINVAL;
   const int R = std::min(7, L - n);
   const bool tc = n == 6 && R == 7;
@@ -1240,8 +1242,16 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
     int8_t sig[16] = {};
     if (!fsv::block_tile_layout(L, n, R, plan[k].lo, plan[(k + 1) % P].lo, &a, sig).empty())
       return SV_EINVAL;
-    uint8_t rows[7] = {1, 2, 4, 8, 16, 32, 64};
-    const int wf = tc ? fsv::block_tc_row_map(sig, rows) : 0;
+    fsv::PassArgs pa;
+    pa.L = L;
+    pa.n = n;
+    pa.R = R;
+    pa.a = a;
+    std::memcpy(pa.sigma, sig, sizeof(sig));
+    const int wf = tc ? fsv::block_tc_layout(pa) : 0;
+    const uint8_t* rows = pa.rowvec;
+    if (staging_out)
+      for (int q = 0; q < 13; ++q) staging_out[13 * k + q] = tc ? (unsigned char)pa.spos[q] : 0;
     if (tile_a) tile_a[k] = a;
     if (sigma_out)
       for (int q = 0; q < 13; ++q) sigma_out[13 * k + q] = q < n + R ? sig[q] : -1;

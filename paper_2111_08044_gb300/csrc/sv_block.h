@@ -44,6 +44,13 @@ struct PassArgs {
   // tensor-core pass: TMEM lane m holds tile row XOR over set bits i of m
   // of rowvec[i] (an invertible map, chosen against staging bank conflicts)
   uint8_t rowvec[7] = {1, 2, 4, 8, 16, 32, 64};
+  // staging order: output tile bit o sits at bit spos[o] of the staging tile
+  // (bits 0-3 fixed: one 128-byte line of the store); the store view's
+  // tile-index coordinates go to dims st_tlo_dim / st_thi_dim (0: none),
+  // shifted by those dims' box bits; st_ndims = 3 for the natural order
+  int8_t spos[13] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12};
+  int8_t ssig[13] = {};  // spos[sigma[k]]: staging bit of window / row bit k
+  int8_t st_ndims = 3, st_tlo_dim = 1, st_tlo_shift = 2, st_thi_dim = 2, st_thi_shift = 7;
   const float2* U = nullptr; // fused unitary, FP32, row-major 2^n x 2^n
   const void* W = nullptr;   // tensor-core operand block of this pass
   void* psi = nullptr;       // state (set at launch)
@@ -107,8 +114,16 @@ size_t block_tc_w_bytes(int n);
 // Row map of a tensor-core pass (n = 6, R = 7) for its relabel sigma: keeps
 // the converters' 128-byte-swizzled row reads conflict-free and spreads each
 // epilogue warp's staging stores over as many banks as sigma allows.
-// Returns the staging wavefronts per warp store (2 is conflict-free).
-int block_tc_row_map(const int8_t* sigma, uint8_t* rowvec);
+// Returns the staging wavefronts per warp store (2 is conflict-free) for the
+// staging order spos.
+int block_tc_row_map(const int8_t* sigma, const int8_t* spos, uint8_t* rowvec);
+// Row map and staging order of a tensor-core pass: the natural staging
+// order unless it leaves a store at 16 wavefronts, in which case the
+// output bits placed at staging bits 4-6 (those the 128-byte swizzle folds
+// into the bank bits) are chosen against the conflicts, with the store view
+// rebuilt from the runs of consecutive state bits.  Fills rowvec, spos and
+// st_*; returns the staging wavefronts per warp store.
+int block_tc_layout(PassArgs& pa);
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);
 
 }  // namespace fsv

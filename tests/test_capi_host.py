@@ -174,17 +174,19 @@ def _block_layout(svlib, L, n):
     rows = np.zeros(64 * 7, np.uint8)
     wf = np.zeros(64, np.int32)
     xs = np.zeros(64, np.int32)
+    st = np.zeros(64 * 13, np.uint8)
     c2 = ctypes.c_int(64)
     assert svlib.sv_host_block_layout(L, ctypes.byref(p), n, ctypes.byref(c2),
                                       a.ctypes.data_as(capi._ip), sig.ctypes.data_as(capi._ip),
                                       rows.ctypes.data, wf.ctypes.data_as(capi._ip),
-                                      xs.ctypes.data_as(capi._ip)) == 0
+                                      xs.ctypes.data_as(capi._ip), st.ctypes.data) == 0
     assert c2.value == P
     los = [lo[k] for k in range(P)]
     # every site's <X> is measured exactly once per period
     measured = [los[k] + j for k in range(P) for j in range(n) if (xs[k] >> j) & 1]
     assert sorted(measured) == list(range(L))
-    return los, a[:P], sig[:13 * P].reshape(P, 13), rows[:7 * P].reshape(P, 7), wf[:P]
+    return (los, a[:P], sig[:13 * P].reshape(P, 13), rows[:7 * P].reshape(P, 7), wf[:P],
+            st[:13 * P].reshape(P, 13))
 
 
 def _site_position(L, n, lo, s):
@@ -199,9 +201,11 @@ def test_block_tile_layout_and_row_map(svlib, L):
     """Each pass's relabel sigma follows the window layout rule; the
     tensor-core row map is invertible, keeps the converter's swizzled row
     reads conflict-free, and its reported staging wavefronts equal a
-    brute-force bank count that never exceeds the natural order's."""
+    brute-force bank count (rows and staging order as chosen) that never
+    exceeds the natural order's; the staging order is a permutation that
+    keeps bits 0-3 and leaves conflict-free passes in the natural order."""
     n, R = 6, min(7, L - 6)
-    los, a, sig, rows, wf = _block_layout(svlib, L, n)
+    los, a, sig, rows, wf, st = _block_layout(svlib, L, n)
     P = len(los)
     for k in range(P):
         lo, lo_next = los[k], los[(k + 1) % P]
@@ -212,8 +216,10 @@ def test_block_tile_layout_and_row_map(svlib, L):
             want = out_pos if out_pos < n else tile_pos.index(out_pos)
             assert sig[k, q] == want, (k, q)
         if R < 7:
-            assert wf[k] == 0 and not rows[k].any()
+            assert wf[k] == 0 and not rows[k].any() and not st[k].any()
             continue
+        assert sorted(st[k]) == list(range(13)) and list(st[k, :4]) == [0, 1, 2, 3]
+        natural = list(st[k]) == list(range(13))
         rmap = [0] * 128
         for m in range(128):
             for i in range(7):
@@ -224,7 +230,7 @@ def test_block_tile_layout_and_row_map(svlib, L):
         for m0 in range(0, 128, 8):
             assert len({rmap[m] & 7 for m in range(m0, m0 + 8)}) == 8
 
-        def wavefronts(rowmap):
+        def wavefronts(rowmap, spos):
             # a 64-bit shared store is served per half-warp: each half takes
             # as many wavefronts as the most lanes on one 8-byte bank slot
             worst = 0
@@ -235,16 +241,17 @@ def test_block_tile_layout_and_row_map(svlib, L):
                         slots = {}
                         for t in range(16 * half, 16 * half + 16):
                             y = c | (rowmap[32 * q + t] << n)
-                            yo = sum(((y >> b) & 1) << int(sig[k, b]) for b in range(13))
+                            yo = sum(((y >> b) & 1) << int(spos[sig[k, b]]) for b in range(13))
                             byte = 8 * yo
                             byte ^= ((byte >> 7) & 7) << 4
                             slots.setdefault((byte >> 3) & 15, set()).add(byte)
                         total += max(len(v) for v in slots.values())
                     worst = max(worst, total)
             return worst
-        got = wavefronts(rmap)
+        got = wavefronts(rmap, st[k])
         assert got == wf[k], (k, got, wf[k])
-        assert got <= wavefronts(list(range(128)))
+        assert got <= wavefronts(list(range(128)), list(range(13)))
+        assert natural or got < 16
     if L == 30:
         # relabels that scattered rows across the banks (natural order: 16,
         # 16, 4, 4 wavefronts) are spread by the row map

@@ -267,13 +267,43 @@ __host__ __device__ constexpr uint32_t make_idesc(int negate_b) {
 // Issued by one elected lane while the whole warp runs the issue loop: the
 // operands are then warp-uniform and the MMAs go out at the tensor pipe's
 // rate (an N = 64 MMA every 32 cycles, against about 50 for a lone lane).
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
+// The 24 MMAs of one k-step (K = 16) into the four accumulators, issued by
+// the lane that `leader` marks (one elect for the whole loop), in one block
+// so that each operand is moved to the issue path once per k-step:
+//   L0re += s0r Ur0 - s0i Ui0         L0im += s0r Ui0 + s0i Ur0   (exact)
+//   Rre  += s0r Ur1 + s1r Ur0 + s0r Ur2 + s1r Ur1 + s2r Ur0
+//         - (s0i Ui1 + s1i Ui0 + s0i Ui2 + s1i Ui1 + s2i Ui0)
+//   Rim  += s0r Ui1 + s1r Ui0 + s0r Ui2 + s1r Ui1 + s2r Ui0
+//         + s0i Ur1 + s1i Ur0 + s0i Ur2 + s1i Ur1 + s2i Ur0
+// (A digit planes s* in TMEM; the B digit matrices U* by descriptor; idesc
+// ip adds, in subtracts; `accumulate` = 0 starts each accumulator).
+__device__ __forceinline__ void mma_kstep(uint32_t leader, uint32_t accumulate, uint32_t l0r,
+                                          uint32_t l0i, uint32_t rr, uint32_t ri, uint32_t r0,
+                                          uint32_t r1, uint32_t r2, uint32_t i0, uint32_t i1,
+                                          uint32_t i2, uint64_t ur0, uint64_t ur1, uint64_t ur2,
+                                          uint64_t ui0, uint64_t ui1, uint64_t ui2, uint32_t ip,
+                                          uint32_t in) {
+#define FSV_MMA(d, a, b, i, p) " @e tcgen05.mma.cta_group::1.kind::f16 [" d "], [" a "], " b ", " i ", " p ";\n"
   asm volatile(
-      "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
-      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      "{\n .reg .pred e, p, t;\n"
+      " setp.ne.b32 e, %0, 0;\n setp.ne.b32 p, %1, 0;\n setp.ne.b32 t, %18, 0;\n"
+      FSV_MMA("%2", "%6", "%12", "%18", "p") FSV_MMA("%2", "%9", "%15", "%19", "t")
+      FSV_MMA("%3", "%6", "%15", "%18", "p") FSV_MMA("%3", "%9", "%12", "%18", "t")
+      FSV_MMA("%4", "%6", "%13", "%18", "p") FSV_MMA("%4", "%7", "%12", "%18", "t")
+      FSV_MMA("%4", "%6", "%14", "%18", "t") FSV_MMA("%4", "%7", "%13", "%18", "t")
+      FSV_MMA("%4", "%8", "%12", "%18", "t") FSV_MMA("%4", "%9", "%16", "%19", "t")
+      FSV_MMA("%4", "%10", "%15", "%19", "t") FSV_MMA("%4", "%9", "%17", "%19", "t")
+      FSV_MMA("%4", "%10", "%16", "%19", "t") FSV_MMA("%4", "%11", "%15", "%19", "t")
+      FSV_MMA("%5", "%6", "%16", "%18", "p") FSV_MMA("%5", "%7", "%15", "%18", "t")
+      FSV_MMA("%5", "%6", "%17", "%18", "t") FSV_MMA("%5", "%7", "%16", "%18", "t")
+      FSV_MMA("%5", "%8", "%15", "%18", "t") FSV_MMA("%5", "%9", "%13", "%18", "t")
+      FSV_MMA("%5", "%10", "%12", "%18", "t") FSV_MMA("%5", "%9", "%14", "%18", "t")
+      FSV_MMA("%5", "%10", "%13", "%18", "t") FSV_MMA("%5", "%11", "%12", "%18", "t")
+      "}\n" ::"r"(leader), "r"(accumulate), "r"(l0r), "r"(l0i), "r"(rr), "r"(ri), "r"(r0),
+      "r"(r1), "r"(r2), "r"(i0), "r"(i1), "r"(i2), "l"(ur0), "l"(ur1), "l"(ur2), "l"(ui0),
+      "l"(ui1), "l"(ui2), "r"(ip), "r"(in)
       : "memory");
+#undef FSV_MMA
 }
 
 // tcgen05.commit from one elected lane of a converged warp
@@ -753,13 +783,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 56;" ::: "memory");
     const uint32_t w0 = sbase + kOffW;
     if (warp == 8) {
-      // the whole warp runs this loop; mma_bf16 / mma_commit issue from one lane
+      // the whole warp runs this loop; the MMAs and commits issue from one lane
       const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
       const uint64_t dr0 = make_desc(w0), dr1 = make_desc(w0 + kMatBytes),
                      dr2 = make_desc(w0 + 2 * kMatBytes), di0 = make_desc(w0 + 3 * kMatBytes),
                      di1 = make_desc(w0 + 4 * kMatBytes), di2 = make_desc(w0 + 5 * kMatBytes);
       constexpr uint32_t ip = make_idesc(0), in = make_idesc(1);
       const uint32_t l0r = tm + kColAcc, l0i = l0r + 64, rr_ = l0r + 128, ri_ = l0r + 192;
+      uint32_t leader;  // the lane that issues the MMAs
+      asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n"
+                   : "=r"(leader));
       bool ok = __all_sync(0xffffffffu, wait_bar(mbase + kBarW, 0, abort, status));
       for (long long i = 0; i < my_tiles && ok; ++i) {
 #pragma unroll 1
@@ -782,32 +815,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                            r2 = ab + kColR2 + 8 * ks;
             const uint32_t i0 = ab + kColI0 + 8 * ks, i1 = ab + kColI1 + 8 * ks,
                            i2 = ab + kColI2 + 8 * ks;
-            // level 0 (exact): s0 u0
-            mma_bf16(l0r, r0, dr0 + ko, ip, acc);
-            mma_bf16(l0r, i0, di0 + ko, in, 1);
-            mma_bf16(l0i, r0, di0 + ko, ip, acc);
-            mma_bf16(l0i, i0, dr0 + ko, ip, 1);
-            // rest: s0 u1 + s1 u0 + s0 u2 + s1 u1 + s2 u0
-            mma_bf16(rr_, r0, dr1 + ko, ip, acc);
-            mma_bf16(rr_, r1, dr0 + ko, ip, 1);
-            mma_bf16(rr_, r0, dr2 + ko, ip, 1);
-            mma_bf16(rr_, r1, dr1 + ko, ip, 1);
-            mma_bf16(rr_, r2, dr0 + ko, ip, 1);
-            mma_bf16(rr_, i0, di1 + ko, in, 1);
-            mma_bf16(rr_, i1, di0 + ko, in, 1);
-            mma_bf16(rr_, i0, di2 + ko, in, 1);
-            mma_bf16(rr_, i1, di1 + ko, in, 1);
-            mma_bf16(rr_, i2, di0 + ko, in, 1);
-            mma_bf16(ri_, r0, di1 + ko, ip, acc);
-            mma_bf16(ri_, r1, di0 + ko, ip, 1);
-            mma_bf16(ri_, r0, di2 + ko, ip, 1);
-            mma_bf16(ri_, r1, di1 + ko, ip, 1);
-            mma_bf16(ri_, r2, di0 + ko, ip, 1);
-            mma_bf16(ri_, i0, dr1 + ko, ip, 1);
-            mma_bf16(ri_, i1, dr0 + ko, ip, 1);
-            mma_bf16(ri_, i0, dr2 + ko, ip, 1);
-            mma_bf16(ri_, i1, dr1 + ko, ip, 1);
-            mma_bf16(ri_, i2, dr0 + ko, ip, 1);
+            mma_kstep(leader, acc, l0r, l0i, rr_, ri_, r0, r1, r2, i0, i1, i2, dr0 + ko, dr1 + ko,
+                      dr2 + ko, di0 + ko, di1 + ko, di2 + ko, ip, in);
           }
           mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
         }

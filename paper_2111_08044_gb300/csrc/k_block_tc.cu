@@ -41,8 +41,10 @@
 //               swizzle (one XOR per amplitude, visiting the row in Gray-code
 //               order), and one TMA tensor store writes the tile back.
 //   warp 8      issues the 96 MMAs of each tile (M=128, N=64, K=16, A in
-//               TMEM, B in shared memory), half by half, from one elected
-//               lane of the converged warp.
+//               TMEM, B in shared memory), half by half, from one lane of
+//               the converged warp elected once; each k-step's 24 MMAs are
+//               one asm block (small code: the kernel is bound by its
+//               instruction cache more than by its issue rate).
 //   warp 9      one thread keeps the TMA producer going: the pass's six
 //               64x64 bf16 digit matrices once, then four 128-row x 128-byte
 //               boxes per tile (cp.async.bulk.tensor.5d, 128-byte swizzle)

@@ -256,6 +256,9 @@ def test_block_tile_layout_and_row_map(svlib, L):
         # relabels that scattered rows across the banks (natural order: 16,
         # 16, 4, 4 wavefronts) are spread by the row map
         assert wf[4] == 4 and wf[5] == 2 and wf[11] == 2 and wf[12] == 2
+        # pass 15 sends six row bits above the bank bits: no row map helps
+        # (16 wavefronts), a reordered staging tile does
+        assert list(st[15]) != list(range(13)) and wf[15] == 2
 
 
 @pytest.mark.parametrize("L,first", [(6, 0), (7, 1)])

@@ -88,8 +88,8 @@ def test_tensor_core_100_periods_with_renormalisation(svlib, L):
 @pytest.mark.parametrize("L,first,ew,periods", [(15, 1, 1.0, 3), (21, 0, 1.0, 2), (26, 1, 0.5, 1)])
 def test_tensor_core_variants_match_oracle(svlib, L, first, ew, periods):
     """Odd L, the other layer order and whole edge fields; at L = 21 the last
-    two passes write through a reordered staging tile (4-D and 5-D store
-    views); at L = 26 the CTAs run 54 tiles each (a ragged tail over 152
+    two passes write through a reordered staging tile (a 4-D store view);
+    at L = 26 the CTAs run 54 tiles each (a ragged tail over 152
     SMs), so the pass instances specialised on what they measure are checked
     element by element."""
     cfg = inputs.ChainConfig(L=L, periods=periods, seed=90 + L, first_layer=first,

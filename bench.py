@@ -279,7 +279,7 @@ def _oracle_periods_per_s(L_sample: int, periods: int, seed: int):
 # DRAM bytes (read + write) of one tensor-core block pass from an ncu
 # capture at L=26 (profiles/k_block_tc_L26.md), per launch; traffic scales
 # with the number of tiles, i.e. with 2^L.
-TC_TRAFFIC_L26 = 1013.2e6
+TC_TRAFFIC_L26 = 1012.8e6
 
 
 def _traffic(args):

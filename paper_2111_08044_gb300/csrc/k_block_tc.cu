@@ -140,6 +140,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // Bounded wait: false on abort (raised here on timeout, or by another role).
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile uint32_t* abort,
                                          int* status) {
+  // the common case first: the phase is already complete
+  if (__builtin_expect(mbar_try_wait(bar, parity), 1)) return true;
   const long long t0 = clock64();
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
@@ -308,12 +310,13 @@ __device__ __forceinline__ void mma_kstep(uint32_t leader, uint32_t accumulate, 
 #undef FSV_MMA
 }
 
-// tcgen05.commit from one elected lane of a converged warp
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
+// tcgen05.commit from the lane that `leader` marks
+__device__ __forceinline__ void mma_commit(uint32_t leader, uint32_t bar) {
   asm volatile(
-      "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
-      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
-          bar)
+      "{\n .reg .pred e;\n setp.ne.b32 e, %0, 0;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%1];\n}\n" ::"r"(
+          leader),
+      "r"(bar)
       : "memory");
 }
 
@@ -820,12 +823,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_kstep(leader, acc, l0r, l0i, rr_, ri_, r0, r1, r2, i0, i1, i2, dr0 + ko, dr1 + ko,
                       dr2 + ko, di0 + ko, di1 + ko, di2 + ko, ip, in);
           }
-          mma_commit(mbase + kBarAFree + 8 * h);  // this half of A may be refilled
+          mma_commit(leader, mbase + kBarAFree + 8 * h);  // this half of A may be refilled
         }
-        if (ok) mma_commit(mbase + kBarDFull);
+        if (ok) mma_commit(leader, mbase + kBarDFull);
       }
       // all issued MMAs complete before TMEM is released
-      mma_commit(mbase + kBarMmaDone);
+      mma_commit(leader, mbase + kBarMmaDone);
       const long long t0 = clock64();
       while (!mbar_try_wait(mbase + kBarMmaDone, 0) && clock64() - t0 < kTimeoutCycles) {
       }

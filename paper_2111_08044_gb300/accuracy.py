@@ -82,6 +82,8 @@ def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64"
     inverse periods back from the product state.  Returns, per P, the
     overlap error |1 - <psi(0)|psi'(0)>| and the relative changes of E and
     sigma_E of psi'(0) against psi(0)."""
+    import time
+    import torch
     cfg = inputs.ChainConfig(L=L, seed=seed)
     sp = cfg.spinors()
     kw = FORMS[form] if precision == "c64" else {}
@@ -91,7 +93,11 @@ def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64"
             sim.init_product_state(sp)
             sim.build(**chain_params(cfg, **kw))
             E0, s0, _ = sim.energy_moments()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             sim.evolve(P, record=False)
+            torch.cuda.synchronize()
+            t_fwd = time.perf_counter() - t0
             sim.build(**chain_params(cfg, inverse=1, **kw))
             sim.evolve(P, record=False)
             ov = sim.overlap_product(sp)
@@ -99,7 +105,7 @@ def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64"
         rows.append({"L": L, "form": form if precision == "c64" else precision, "periods": P,
                      "total_time": 2 * P * cfg.T, "overlap_error": abs(1.0 - ov),
                      "rel_err_E": abs(E1 - E0) / abs(E0), "rel_err_sigma": abs(s1 - s0) / s0,
-                     "norm_dev": n1 - 1.0})
+                     "norm_dev": n1 - 1.0, "s_per_period_forward": t_fwd / P})
     return rows
 
 

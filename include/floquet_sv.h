@@ -358,6 +358,26 @@ int sv_host_block_layout(int L, const sv_floquet_params *p, int n, int *n_passes
                          int *store_wavefronts, int *x_sites_out,
                          unsigned char *staging_out);
 
+/* Host only, no device work: the TMA store view of tensor-core pass `pass`
+ * (n = 6, L >= 13) of the fusion plan for (L, *p) -- the layout the pass's
+ * 64 KiB staging tile is written back through.  Outputs:
+ *   *rank                     3 to 5 (dimension 0 plus one per run of the
+ *                             staging order);
+ *   dims[5], box[5]           extents in amplitudes (8-byte elements) of
+ *                             the view and of the stored box (1 past rank);
+ *   strides[4]                byte strides of dimensions 1..rank-1;
+ *   coord[4]                  tile t = tlo + 2^(a-6) thi is stored at
+ *                             coordinate tlo << coord[1] of dimension
+ *                             coord[0] and thi << coord[3] of dimension
+ *                             coord[2], all other coordinates 0.
+ * Staging element s (box order, dimension 0 fastest) of tile t lands at
+ * amplitude sum_d (c_d + i_d) strides_d / 8.  Ownership: caller buffers.
+ * Errors: SV_EINVAL (bad arguments, pass out of range, not a tensor-core
+ * width). */
+int sv_host_store_view(int L, const sv_floquet_params *p, int n, int pass, int *rank,
+                       unsigned long long *dims, unsigned long long *strides, unsigned *box,
+                       int *coord);
+
 /* ------------------------------------------------------------------ batch
  * Many independent chains (each its own L, parameters and product state)
  * evolved together on one device.  Chains of up to 14 sites can stay in one

@@ -102,6 +102,7 @@ SIGNATURES = {
     "sv_init_pairs": ([_vp, _i32, _dp], _i32),
     "sv_overlap_pairs": ([_vp, _dp, _dp, _dp], _i32),
     "sv_host_block_layout": ([_i32, _pp, _i32, _ip, _ip, _ip, _vp, _ip, _ip, _vp], _i32),
+    "sv_host_store_view": ([_i32, _pp, _i32, _i32, _ip, _vp, _vp, _vp, _ip], _i32),
     "sv_batch_state_bytes": ([_i32, _ip], _sz),
     "sv_batch_create": ([ctypes.POINTER(_vp), _i32, _i32, _ip, _pp, _dp, _vp, _sz, _i32, _vp],
                         _i32),

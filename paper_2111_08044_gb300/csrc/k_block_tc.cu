@@ -1155,6 +1155,28 @@ void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out
   std::memcpy(out.data(), h.data(), kWBytes);
 }
 
+int block_tc_store_view(const PassArgs& pa, uint64_t* dims, uint64_t* strides, uint32_t* box) {
+  int first[9], len[9];
+  const int a = pa.a, L = pa.L;
+  const int nr = store_runs(pa.spos, a, first, len);
+  if (nr > 4 || nr + 1 != pa.st_ndims) return -1;
+  for (int d = 0; d < 5; ++d) {
+    dims[d] = d == 0 ? 16 : 1;
+    box[d] = d == 0 ? 16 : 1;
+  }
+  for (int d = 0; d < 4; ++d) strides[d] = 0;
+  for (int k = 0; k < nr; ++k) {
+    const int last = first[k] + len[k] - 1;
+    int bits = len[k];
+    if (last == kN - 1) bits += a - kN;
+    if (last == 12) bits += L - a - 7;
+    dims[k + 1] = (uint64_t)1 << bits;
+    strides[k] = (uint64_t)8 << out_state_bit(first[k], a);
+    box[k + 1] = 1u << len[k];
+  }
+  return nr + 1;
+}
+
 // Two descriptors per pass: the load view (tile rows as 128-row boxes of
 // 128 bytes: window amplitudes 16 c .. 16 c + 15 of each row) and the store
 // view of the staging order: amplitudes 0-15 of an output row, then one
@@ -1175,21 +1197,11 @@ int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) return SV_ECUDA;
   // store view: 8-byte elements (one complex amplitude each)
-  int first[9], len[9];
-  const int nr = store_runs(pa.spos, a, first, len);
-  if (nr > 4 || nr + 1 != pa.st_ndims) return SV_EINVAL;
-  cuuint64_t odims[5] = {16, 1, 1, 1, 1}, ostrides[4] = {0, 0, 0, 0};
-  cuuint32_t obox[5] = {16, 1, 1, 1, 1};
-  for (int k = 0; k < nr; ++k) {
-    const int last = first[k] + len[k] - 1;
-    int bits = len[k];
-    if (last == kN - 1) bits += a - kN;
-    if (last == 12) bits += L - a - 7;
-    odims[k + 1] = (cuuint64_t)1 << bits;
-    ostrides[k] = (cuuint64_t)8 << out_state_bit(first[k], a);
-    obox[k + 1] = 1u << len[k];
-  }
-  rc = fn(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, nr + 1, psi, odims, ostrides, obox, estr,
+  uint64_t odims[5], ostrides[4];
+  uint32_t obox[5];
+  const int rank = block_tc_store_view(pa, odims, ostrides, obox);
+  if (rank < 0) return SV_EINVAL;
+  rc = fn(&maps[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, rank, psi, odims, ostrides, obox, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (rc != CUDA_SUCCESS) return SV_ECUDA;

@@ -1267,4 +1267,39 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
   return SV_OK;
 }
 
+int sv_host_store_view(int L, const sv_floquet_params* p, int n, int pass, int* rank,
+                       unsigned long long* dims, unsigned long long* strides, unsigned* box,
+                       int* coord) {
+  if (!p || !rank || !dims || !strides || !box || !coord) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  if (!fsv::block_tc_supported(L, n)) return SV_EINVAL;
+  auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
+  auto plan = fsv::fusion_plan(L, gates, n);
+  const int P = (int)plan.size();
+  if (pass < 0 || pass >= P) return SV_EINVAL;
+  fsv::PassArgs pa;
+  pa.L = L;
+  pa.n = n;
+  pa.R = 7;
+  if (!fsv::block_tile_layout(L, n, 7, plan[pass].lo, plan[(pass + 1) % P].lo, &pa.a, pa.sigma)
+           .empty())
+    return SV_EINVAL;
+  fsv::block_tc_layout(pa);
+  uint64_t d[5], st[4];
+  uint32_t b[5];
+  const int r = fsv::block_tc_store_view(pa, d, st, b);
+  if (r < 0) return SV_EINVAL;
+  *rank = r;
+  for (int k = 0; k < 5; ++k) {
+    dims[k] = d[k];
+    box[k] = b[k];
+  }
+  for (int k = 0; k < 4; ++k) strides[k] = st[k];
+  coord[0] = pa.st_tlo_dim;
+  coord[1] = pa.st_tlo_shift;
+  coord[2] = pa.st_thi_dim;
+  coord[3] = pa.st_thi_shift;
+  return SV_OK;
+}
+
 }  // extern "C"

@@ -124,6 +124,11 @@ int block_tc_row_map(const int8_t* sigma, const int8_t* spos, uint8_t* rowvec);
 // rebuilt from the runs of consecutive state bits.  Fills rowvec, spos and
 // st_*; returns the staging wavefronts per warp store.
 int block_tc_layout(PassArgs& pa);
+// The store view of a tensor-core pass (after block_tc_layout): dimension 0
+// is 16 amplitudes, then one dimension per run of the staging order; dims,
+// byte strides of dimensions 1.. and box extents.  Returns the rank (3-5),
+// -1 if the staging order needs more dimensions than a tensor map has.
+int block_tc_store_view(const PassArgs& pa, uint64_t* dims, uint64_t* strides, uint32_t* box);
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);
 
 }  // namespace fsv

@@ -286,3 +286,71 @@ def test_inverse_flag_checks(svlib):
     assert svlib.sv_host_period_gates(6, ctypes.byref(p), ctypes.byref(n), None, None) == capi.SV_EINVAL
     p, _ = capi.make_params(inverse=1, theta_p=[0.1, 0.2])
     assert svlib.sv_host_period_gates(6, ctypes.byref(p), ctypes.byref(n), None, None) == capi.SV_EINVAL
+
+
+def _store_view(svlib, L, p, k):
+    rank = ctypes.c_int(0)
+    dims = (ctypes.c_ulonglong * 5)()
+    strides = (ctypes.c_ulonglong * 4)()
+    box = (ctypes.c_uint * 5)()
+    coord = (ctypes.c_int * 4)()
+    assert svlib.sv_host_store_view(L, ctypes.byref(p), 6, k, ctypes.byref(rank), dims, strides,
+                                    box, coord) == 0
+    r = rank.value
+    return r, list(dims)[:r], [8] + list(strides)[:r - 1], list(box)[:r], list(coord)
+
+
+@pytest.mark.parametrize("L,first", [(13, 0), (14, 0), (19, 0), (21, 0), (21, 1), (27, 0), (30, 0)])
+def test_tensor_core_store_view_places_every_amplitude(svlib, L, first):
+    """The TMA store view of every tensor-core pass, walked on the host: the
+    staging element that holds output amplitude y of tile t (staging bit
+    spos[o] = output bit o) lands on the state index the pass writes, i.e.
+    output bits 0-5 on state bits 0-5, output bits 6-12 on state bits
+    a..a+6 and the tile index on the bits between and above; the view
+    covers 2^L amplitudes and each box lies inside it.  Reordered staging
+    tiles (4-D and 5-D views) are included."""
+    n = 6
+    p, _ = capi.make_params(first_layer=first)
+    cnt = ctypes.c_int(64)
+    a = np.zeros(64, np.int32)
+    st = np.zeros(64 * 13, np.uint8)
+    assert svlib.sv_host_block_layout(L, ctypes.byref(p), n, ctypes.byref(cnt),
+                                      a.ctypes.data_as(capi._ip), None, None, None, None,
+                                      st.ctypes.data) == 0
+    P = cnt.value
+    bad = ctypes.c_int(0)
+    assert svlib.sv_host_store_view(L, ctypes.byref(p), n, P, ctypes.byref(bad),
+                                    (ctypes.c_ulonglong * 5)(), (ctypes.c_ulonglong * 4)(),
+                                    (ctypes.c_uint * 5)(), (ctypes.c_int * 4)()) == capi.SV_EINVAL
+    s = np.arange(1 << 13, dtype=np.int64)
+    restaged = 0
+    for k in range(P):
+        ak = int(a[k])
+        spos = [int(v) for v in st[13 * k:13 * k + 13]]
+        restaged += spos != list(range(13))
+        rank, dims, strides, box, coord = _store_view(svlib, L, p, k)
+        assert int(np.prod(dims)) == 1 << L and int(np.prod(box)) == 1 << 13
+        # output index held by staging element s, and its state bits
+        y = np.zeros_like(s)
+        for o in range(13):
+            y |= ((s >> spos[o]) & 1) << o
+        x_in = np.zeros_like(s)
+        for o in range(13):
+            x_in |= ((y >> o) & 1) << (o if o < n else ak + o - n)
+        # box indices of s, dimension 0 fastest
+        idx, rest = [], s.copy()
+        for d in range(rank):
+            idx.append(rest % box[d])
+            rest //= box[d]
+        ntlo, nthi = 1 << (ak - n), 1 << (L - ak - 7)
+        for t in sorted({0, min(1, ntlo * nthi - 1), ntlo * nthi - 1, (ntlo * nthi) // 3}):
+            tlo, thi = t % ntlo, t // ntlo
+            c = [0] * rank
+            c[coord[0]] |= tlo << coord[1]
+            c[coord[2]] |= thi << coord[3]
+            assert all(c[d] + box[d] <= dims[d] for d in range(rank)), (k, t)
+            addr = sum((c[d] + idx[d]) * strides[d] for d in range(rank))
+            want = 8 * (x_in | (tlo << n) | (thi << (ak + 7)))
+            np.testing.assert_array_equal(addr, want, err_msg=f"pass {k} tile {t}")
+    if (L, first) in ((21, 0), (30, 0)):
+        assert restaged > 0

@@ -204,7 +204,7 @@ def pair_ground_states(h_bonds: np.ndarray, L: int) -> np.ndarray:
 
 @dataclass
 class CircuitConfig:
-    """The paper's random Floquet circuit (Sec. III): L qubits, GUE bond
+    """The paper's random Floquet circuit (Sec. III.A): L qubits, GUE bond
     terms H_k, gates exp(-i H_k T), the layer of the paper's even bonds
     (0-based odd bonds) first, no kick, drive frequency omega = 2 pi / T,
     started from the dimer-product state of Eq. 9."""

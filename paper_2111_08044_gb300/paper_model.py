@@ -1,7 +1,10 @@
-"""The paper's own experiment (Sec. III): the random Floquet circuit of GUE
-bond terms, started from the dimer-product state of Eq. 9, with the energy
+"""The paper's own experiment (Sec. IV, on the model of Sec. III.A): the
+random Floquet circuit of GUE bond terms, started from the dimer-product
+state of Eq. 9, with the energy
 E(t) = <H_bar> and its spread sigma_E(t) (Eq. 10, Eq. 11) recorded at
-log-spaced times for several drive frequencies omega = 2 pi / T.
+log-spaced times for several drive frequencies omega = 2 pi / T, and the
+heating rate Gamma = 1/(t_2 - t_1) with E(t_k) = E(0) e^-k, fitted to
+Gamma = exp(a omega + b) across the frequencies (Sec. IV).
 
 The sample of bond terms is a seeded stand-in for the paper's (not
 available).  The infinite-temperature references are E_inf = 0 (the terms
@@ -38,6 +41,44 @@ def sigma_infinite_temperature(h: np.ndarray) -> float:
     return math.sqrt(s)
 
 
+def crossing_time(t, ratio, k: int):
+    """The time t_k at which E(t)/E(0) first falls to e^-k (Sec. IV: E
+    relaxes from E(0) < 0 towards the infinite-temperature value 0), by
+    linear interpolation in log t between the two samples that bracket it
+    (the samples are log-spaced); None if the curve never gets there."""
+    level = math.exp(-k)
+    t = np.asarray(t, dtype=float)
+    r = np.asarray(ratio, dtype=float)
+    if r[0] <= level:
+        return float(t[0])
+    for i in range(1, len(t)):
+        if r[i] > level:
+            continue
+        w = (r[i - 1] - level) / (r[i - 1] - r[i])  # r[i - 1] > level >= r[i]
+        if t[i - 1] <= 0.0:  # the first sample is t = 0
+            return float(t[i - 1] + w * (t[i] - t[i - 1]))
+        return float(math.exp(math.log(t[i - 1]) + w * (math.log(t[i]) - math.log(t[i - 1]))))
+    return None
+
+
+def heating_rate(t, energy):
+    """Gamma = 1 / (t_2 - t_1), the paper's thermalization rate (Sec. IV),
+    from the energy curve E(t) with E(0) = energy[0]; None if E(t) does not
+    reach E(0) e^-2 within the run."""
+    r = np.asarray(energy, dtype=float) / float(energy[0])
+    t1, t2 = crossing_time(t, r, 1), crossing_time(t, r, 2)
+    if t1 is None or t2 is None or t2 <= t1:
+        return None
+    return 1.0 / (t2 - t1)
+
+
+def fit_rates(omegas, rates):
+    """Least-squares fit of log Gamma = a omega + b (the paper's exponential
+    suppression of heating in the drive frequency); returns (a, b)."""
+    a, b = np.polyfit(np.asarray(omegas, dtype=float), np.log(np.asarray(rates, dtype=float)), 1)
+    return float(a), float(b)
+
+
 def run(L: int, omega: float, t_max: float, points: int = 24, seed: int = 11,
         block: bool = True):
     """Rows {t, periods, E, E/L, sigma_E, norm} from the dimer-product state."""
@@ -71,10 +112,18 @@ def main():
     h = inputs.gue_bond_terms(a.L - 1, a.seed)
     ref = dict(L=a.L, E_inf=0.0, sigma_inf=sigma_infinite_temperature(h))
     print(json.dumps(ref), flush=True)
+    got = []
     for w in (float(x) for x in a.omega.split(",")):
         cfg, rows = run(a.L, w, a.tmax, a.points, a.seed, not a.plain)
         for r in rows:
             print(json.dumps(dict(omega=w, T=cfg.T, **r)), flush=True)
+        g = heating_rate([r["t"] for r in rows], [r["E"] for r in rows])
+        print(json.dumps(dict(omega=w, heating_rate=g)), flush=True)
+        if g is not None:
+            got.append((w, g))
+    if len(got) >= 2:
+        fa, fb = fit_rates([w for w, _ in got], [g for _, g in got])
+        print(json.dumps(dict(fit="log Gamma = a omega + b", a=fa, b=fb, points=len(got))), flush=True)
 
 
 if __name__ == "__main__":

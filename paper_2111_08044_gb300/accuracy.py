@@ -20,6 +20,11 @@ then the overlap error |1 - <psi(0)|psi'(0)>| and the relative changes of E
 and sigma_E (Eq. 10-11) between psi(0) and psi'(0):
 
     python -m paper_2111_08044_gb300.accuracy --echo --L 26 --periods 10,100,1000
+
+and on the paper's own random circuit from its dimer state (omega = 8 as in
+Sec. V):
+
+    python -m paper_2111_08044_gb300.accuracy --echo --circuit --L 34 --periods 10 --forms block_tc
 """
 from __future__ import annotations
 
@@ -77,33 +82,61 @@ def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
     return rows
 
 
-def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64"):
+def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64",
+         circuit=False, omega=8.0):
     """The echo of Sec. V for each P in `periods`: P periods forward and P
-    inverse periods back from the product state.  Returns, per P, the
-    overlap error |1 - <psi(0)|psi'(0)>| and the relative changes of E and
-    sigma_E of psi'(0) against psi(0)."""
+    inverse periods back.  The start is the Ising chain's product state, or
+    with `circuit` the paper's own random circuit (GUE bonds, drive
+    frequency omega) from its dimer-product state, as in Sec. V.  Returns,
+    per P, the overlap error |1 - <psi(0)|psi'(0)>| and the relative
+    changes of E and sigma_E of psi'(0) against psi(0)."""
     import time
     import torch
-    cfg = inputs.ChainConfig(L=L, seed=seed)
-    sp = cfg.spinors()
     kw = FORMS[form] if precision == "c64" else {}
+    if circuit:
+        ccfg = inputs.CircuitConfig(L=L, omega=omega, seed=seed)
+        start = ccfg.pair_states()
+        period_T = ccfg.T
+
+        def prepare(sim, inverse):
+            sim.build(**dict(ccfg.build_kwargs(), inverse=inverse, **kw))
+
+        def init(sim):
+            sim.init_pairs(start)
+
+        def overlap(sim):
+            return sim.overlap_pairs(start)
+    else:
+        cfg = inputs.ChainConfig(L=L, seed=seed)
+        start = cfg.spinors()
+        period_T = cfg.T
+
+        def prepare(sim, inverse):
+            sim.build(**chain_params(cfg, inverse=inverse, **kw))
+
+        def init(sim):
+            sim.init_product_state(start)
+
+        def overlap(sim):
+            return sim.overlap_product(start)
     rows = []
     for P in periods:
         with FloquetSimulator(L, precision=precision) as sim:
-            sim.init_product_state(sp)
-            sim.build(**chain_params(cfg, **kw))
+            init(sim)
+            prepare(sim, 0)
             E0, s0, _ = sim.energy_moments()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             sim.evolve(P, record=False)
             torch.cuda.synchronize()
             t_fwd = time.perf_counter() - t0
-            sim.build(**chain_params(cfg, inverse=1, **kw))
+            prepare(sim, 1)
             sim.evolve(P, record=False)
-            ov = sim.overlap_product(sp)
+            ov = overlap(sim)
             E1, s1, n1 = sim.energy_moments()
-        rows.append({"L": L, "form": form if precision == "c64" else precision, "periods": P,
-                     "total_time": 2 * P * cfg.T, "overlap_error": abs(1.0 - ov),
+        rows.append({"L": L, "model": "circuit" if circuit else "ising",
+                     "form": form if precision == "c64" else precision, "periods": P,
+                     "total_time": 2 * P * period_T, "overlap_error": abs(1.0 - ov),
                      "rel_err_E": abs(E1 - E0) / abs(E0), "rel_err_sigma": abs(s1 - s0) / s0,
                      "norm_dev": n1 - 1.0, "s_per_period_forward": t_fwd / P})
     return rows
@@ -118,11 +151,14 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--forms", default="plain,block_tc")
     ap.add_argument("--echo", action="store_true")
+    ap.add_argument("--circuit", action="store_true",
+                    help="echo the paper's random circuit from its dimer state")
+    ap.add_argument("--omega", type=float, default=8.0, help="drive frequency (--circuit)")
     a = ap.parse_args()
     if a.echo:
         ps = tuple(int(x) for x in a.periods.split(","))
         for form in a.forms.split(","):
-            for row in echo(a.L, ps, a.seed, form):
+            for row in echo(a.L, ps, a.seed, form, circuit=a.circuit, omega=a.omega):
                 print(json.dumps(row), flush=True)
         return
     for row in study(a.L, int(a.periods), a.every, a.seed, tuple(a.forms.split(","))):

@@ -322,6 +322,11 @@ def test_tensor_core_store_view_places_every_amplitude(svlib, L, first):
     assert svlib.sv_host_store_view(L, ctypes.byref(p), n, P, ctypes.byref(bad),
                                     (ctypes.c_ulonglong * 5)(), (ctypes.c_ulonglong * 4)(),
                                     (ctypes.c_uint * 5)(), (ctypes.c_int * 4)()) == capi.SV_EINVAL
+    for badL, badn in ((L, 5), (12, 6)):  # not a tensor-core width / too short
+        assert svlib.sv_host_store_view(badL, ctypes.byref(p), badn, 0, ctypes.byref(bad),
+                                        (ctypes.c_ulonglong * 5)(), (ctypes.c_ulonglong * 4)(),
+                                        (ctypes.c_uint * 5)(),
+                                        (ctypes.c_int * 4)()) == capi.SV_EINVAL
     s = np.arange(1 << 13, dtype=np.int64)
     restaged = 0
     for k in range(P):

@@ -291,9 +291,12 @@ void sv_destroy(sv_ctx *ctx);
  * first call on a device looks that array up on the current device, so
  * make the first call before any stream capture.  Every call reuses the
  * same array (zeroing it first), so calls that overlap on the GPU race: do
- * not run two at once.  Returns without synchronising.  Errors: SV_EINVAL
- * (null pointer, bad precision, L beyond the limit, invalid parameters),
- * SV_ECUDA (symbol lookup or launch failed).
+ * not run two at once.  It measures the driven Ising chain's H0 only: a
+ * chain given by general bond terms (p->h_bonds set; its observable is
+ * sum_b H_b, Eq. 7) is refused, use sv_expect_energy for it.  Returns
+ * without synchronising.  Errors: SV_EINVAL (null pointer, bad precision,
+ * L beyond the limit, invalid parameters, p->h_bonds set), SV_ECUDA
+ * (symbol lookup or launch failed).
  */
 int sv_energy_noalloc(const void *psi_dev, int L, int precision,
                       const sv_floquet_params *p, double *out_dev, void *cuda_stream);
@@ -330,6 +333,21 @@ int sv_host_period_gates(int L, const sv_floquet_params *p, int *n_gates,
  */
 int sv_host_fusion_plan(int L, const sv_floquet_params *p, int n, int *n_passes,
                         int *window_lo, int *gate_count, double *unitaries_out);
+
+/*
+ * The operand a block pass applies in place of pass `pass`'s fused unitary
+ * (see sv_host_fusion_plan): the fused 2^n x 2^n unitary of the window as
+ * the pass's number format represents it, chosen entry by entry between the
+ * two representable values bracketing the exact entry so that the matrix is
+ * as close to unitary as the format allows (the same operand is applied
+ * every period, so a defect U^H U - I would change the norm by the same
+ * amount every period).  split = SV_SPLIT_FP32: the CUDA-core pass's FP32
+ * entries; SV_SPLIT_BF16X3 (n = 6): the value of the tensor-core pass's
+ * three digits u = 2^-7 (u0 + u1/256 + u2/65536).  operand_out: 2*4^n
+ * doubles, row-major complex.  Errors: SV_EINVAL.
+ */
+int sv_host_pass_operand(int L, const sv_floquet_params *p, int n, int pass, int split,
+                         double *operand_out);
 
 /*
  * Block-mode tile layout of each pass (the relabel of Sec. II's qubit

@@ -101,6 +101,7 @@ SIGNATURES = {
     "sv_overlap_product": ([_vp, _dp, _dp, _dp], _i32),
     "sv_init_pairs": ([_vp, _i32, _dp], _i32),
     "sv_overlap_pairs": ([_vp, _dp, _dp, _dp], _i32),
+    "sv_host_pass_operand": ([_i32, _pp, _i32, _i32, _i32, _dp], _i32),
     "sv_host_block_layout": ([_i32, _pp, _i32, _ip, _ip, _ip, _vp, _ip, _ip, _vp], _i32),
     "sv_host_store_view": ([_i32, _pp, _i32, _i32, _ip, _vp, _vp, _vp, _ip], _i32),
     "sv_batch_state_bytes": ([_i32, _ip], _sz),

@@ -366,6 +366,14 @@ std::vector<AdjOp> adjoint_period_ops(int L, const sv_floquet_params &p, double 
   return ops;
 }
 
+double site_field_share(int L, int i, double ew) {
+  // the bonds (i-1, i) and (i, i+1) each give site i its share of the fields
+  double w = 0.0;
+  if (i >= 1) w += field_share(L, i - 1, 1, ew);
+  if (i + 1 <= L - 1) w += field_share(L, i, 0, ew);
+  return w;
+}
+
 Observable observable(int L, const sv_floquet_params &p) {
   Observable o;
   o.L = L;
@@ -378,12 +386,11 @@ Observable observable(int L, const sv_floquet_params &p) {
   o.J = p.J;
   o.cx.assign(L, 0.0);
   o.cz.assign(L, 0.0);
-  for (int b = 0; b < L - 1; ++b)
-    for (int side = 0; side < 2; ++side) {
-      double w = field_share(L, b, side, p.edge_field_weight);
-      o.cx[b + side] += p.hx * w;
-      o.cz[b + side] += p.hz * w;
-    }
+  for (int i = 0; i < L; ++i) {
+    const double w = site_field_share(L, i, p.edge_field_weight);
+    o.cx[i] = p.hx * w;
+    o.cz[i] = p.hz * w;
+  }
   return o;
 }
 

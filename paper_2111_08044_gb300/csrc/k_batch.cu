@@ -58,16 +58,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         float2 w[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-          float2 a = czero<float2>(), lo = czero<float2>();
+          // residual products first, then the table's on top: a bare first
+          // product with a fixed table entry would bias the norm downwards
+          float2 a = czero<float2>();
+          a = cmac(a, Gl[4 * r + 0], v0);
+          a = cmac(a, Gl[4 * r + 1], v1);
+          a = cmac(a, Gl[4 * r + 2], v2);
+          a = cmac(a, Gl[4 * r + 3], v3);
           a = cmac(a, G[4 * r + 0], v0);
           a = cmac(a, G[4 * r + 1], v1);
           a = cmac(a, G[4 * r + 2], v2);
           a = cmac(a, G[4 * r + 3], v3);
-          lo = cmac(lo, Gl[4 * r + 0], v0);
-          lo = cmac(lo, Gl[4 * r + 1], v1);
-          lo = cmac(lo, Gl[4 * r + 2], v2);
-          lo = cmac(lo, Gl[4 * r + 3], v3);
-          w[r] = make_float2(a.x + lo.x, a.y + lo.y);
+          w[r] = a;
         }
         sp[x] = w[0];
         sp[x + o1] = w[1];

@@ -65,9 +65,20 @@ __global__ void __launch_bounds__(kSimtThreads) k_block_simt(float2* __restrict_
       const int item = threadIdx.x + it * blockDim.x;
       rr[it] = item % rows;
       cb[it] = item / rows;
+      // each output starts from its row's largest entry's FP32 residual
+      // times that entry's amplitude: a sum started from a bare product
+      // with a fixed entry rounds with an error that correlates with the
+      // result (for passes of few gates, with one dominant entry per row,
+      // it biased the norm by 1e-8 per period); the residual term varies
+      // independently of that rounding grid and takes the bias out
 #pragma unroll
       for (int j = 0; j < CH; ++j) acc[it][j] = make_float2(0.f, 0.f);
       if (item < nitems) {
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const float4 ld = __ldg(&pa.Ulead[cb[it] * CH + j]);
+          acc[it][j] = cmac(acc[it][j], make_float2(ld.x, ld.y), tile[rr[it] * DP + (int)ld.z]);
+        }
         for (int k = 0; k < D; ++k) {
           const float2 v = tile[rr[it] * DP + k];
 #pragma unroll
@@ -272,14 +283,21 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   bp->nslots = slot;
   // device buffers
   const size_t dim = (size_t)1 << n;
-  std::vector<float2> hu((size_t)P * dim * dim);
-  for (int k = 0; k < P; ++k)
-    for (size_t e = 0; e < dim * dim; ++e)
-      hu[k * dim * dim + e] = make_float2((float)bp->passes[k].U[e].real(),
-                                          (float)bp->passes[k].U[e].imag());
-  if (cudaMalloc(&bp->d_U, sizeof(float2) * hu.size()) != cudaSuccess ||
-      cudaMemcpy(bp->d_U, hu.data(), sizeof(float2) * hu.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess) {
+  std::vector<float2> hu(bp->tensor_cores ? 0 : (size_t)P * dim * dim);
+  std::vector<float4> hl(bp->tensor_cores ? 0 : (size_t)P * dim);
+  std::vector<std::vector<uint32_t>> hw(bp->tensor_cores ? P : 0);
+  // the operands of every pass, rounded close to unitary (host_round.cpp)
+  round_passes_parallel(P, [&](int k) {
+    if (bp->tensor_cores) block_tc_pack_w(n, bp->passes[k].U, hw[k]);
+    else round_unitary_fp32((int)dim, bp->passes[k].U.data(), &hu[k * dim * dim], &hl[k * dim]);
+  });
+  if (!bp->tensor_cores &&
+      (cudaMalloc(&bp->d_U, sizeof(float2) * hu.size()) != cudaSuccess ||
+       cudaMemcpy(bp->d_U, hu.data(), sizeof(float2) * hu.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess ||
+       cudaMalloc(&bp->d_Ulead, sizeof(float4) * hl.size()) != cudaSuccess ||
+       cudaMemcpy(bp->d_Ulead, hl.data(), sizeof(float4) * hl.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess)) {
     cudaGetLastError();
     *msg = "unitary upload failed";
     block_free(bp);
@@ -287,12 +305,8 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   }
   if (bp->tensor_cores) {
     bp->w_bytes_per_pass = block_tc_w_bytes(n);
-    std::vector<uint32_t> hw;
     std::vector<uint32_t> all;
-    for (int k = 0; k < P; ++k) {
-      block_tc_pack_w(n, bp->passes[k].U, hw);
-      all.insert(all.end(), hw.begin(), hw.end());
-    }
+    for (int k = 0; k < P; ++k) all.insert(all.end(), hw[k].begin(), hw[k].end());
     if (cudaMalloc(&bp->d_W, all.size() * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemcpy(bp->d_W, all.data(), all.size() * sizeof(uint32_t),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -312,7 +326,10 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   }
   for (int k = 0; k < P; ++k) {
     PassArgs& pa = bp->args[k];
-    pa.U = bp->d_U + (size_t)k * dim * dim;
+    if (bp->d_U) {
+      pa.U = bp->d_U + (size_t)k * dim * dim;
+      pa.Ulead = bp->d_Ulead + (size_t)k * dim;
+    }
     if (bp->d_W)
       pa.W = static_cast<const char*>(bp->d_W) + (size_t)k * bp->w_bytes_per_pass;
     if (pa.slot >= 0) pa.partial = bp->d_partials + 2 * (size_t)pa.slot * bp->maxb;
@@ -347,7 +364,9 @@ void block_info(const BlockPlan* bp, int* passes, int* launches) {
 
 size_t block_upload_bytes(const BlockPlan* bp) {
   const size_t P = bp->passes.size();
-  return P * sizeof(float2) * ((size_t)1 << (2 * bp->n)) + P * bp->w_bytes_per_pass;
+  const size_t dim = (size_t)1 << bp->n;
+  const size_t u = bp->tensor_cores ? 0 : sizeof(float2) * dim * dim + sizeof(float4) * dim;
+  return P * (u + bp->w_bytes_per_pass);
 }
 
 namespace {
@@ -417,6 +436,7 @@ cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* cou
 void block_free(BlockPlan* bp) {
   if (!bp) return;
   cudaFree(bp->d_U);
+  cudaFree(bp->d_Ulead);
   cudaFree(bp->d_W);
   cudaFree(bp->d_partials);
   cudaFree(bp->d_status);

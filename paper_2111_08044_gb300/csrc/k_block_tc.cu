@@ -13,7 +13,12 @@
 //     residual is below 2^-25 of 2^e_r, finer than FP32 rounding of the
 //     row's largest entry);
 //   - each entry of the fused unitary likewise, u = 2^-7 (u0 + u1/256 +
-//     u2/65536);
+//     u2/65536), u0 an integer and u1, u2 with 8 significant bits (bf16
+//     values; only u0 must be an integer for the exact level-0 sum), the
+//     last digit chosen between its two neighbours so that the represented
+//     matrix is as close to unitary as the digits allow (a nearest rounding
+//     leaves a defect that changes the norm by the same amount every
+//     period);
 //   - the digits are held as exact bf16 values at their true scale, so the
 //     s0 u0 products are integers below 2^14 in units of 2^(e_r-14), and
 //     their sum over K = 64 (both complex parts) stays below 2^21 units:
@@ -899,9 +904,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-uint16_t bf16_of_int(double v, double scale) {
-  // v is an integer with |v| <= 256 and scale a power of two: v * scale is
-  // exact in bf16 and in float
+uint16_t bf16_of(double v, double scale) {
+  // v has at most 8 significant bits and scale is a power of two: v * scale
+  // is exact in float and in bf16 (the low 16 bits of the float are zero)
   float f = (float)(v * scale);
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -1128,26 +1133,25 @@ int block_tc_layout(PassArgs& pa) {
 
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out) {
   // six K-major 64 x 64 bf16 digit matrices Ur0, Ur1, Ur2, Ui0, Ui1, Ui2
-  // holding u0/128, u1/32768, u2/2^23 with u = 2^-7 (u0 + u1/256 + u2/65536),
-  // |u_t| <= 128, in the core-matrix order
-  // of make_desc: element (row j, col k) at halfword
-  // ((k/8)*8 + j/8)*64 + (j%8)*8 + k%8
+  // holding u0/128, u1/32768, u2/2^23 with u = 2^-7 (u0 + u1/256 + u2/65536)
+  // (u0 an integer, |u_t| <= 128; the digits chosen by round_unitary_digits
+  // so that the represented matrix is as close to unitary as they allow),
+  // in the core-matrix order of make_desc: element (row j, col k) at
+  // halfword ((k/8)*8 + j/8)*64 + (j%8)*8 + k%8
   out.assign(kWBytes / 4, 0u);
   if (n != kN) return;
+  std::vector<double> dg((size_t)6 * kCols * kCols);
+  round_unitary_digits(kCols, U.data(), dg.data());
   std::vector<uint16_t> h(kWBytes / 2, 0);
   const size_t m = (size_t)kCols * kCols;
   for (int j = 0; j < kCols; ++j)
     for (int k = 0; k < kCols; ++k) {
-      const cd u = U[(size_t)j * kCols + k];
+      const size_t e = (size_t)j * kCols + k;
       const size_t w = (size_t)(((k >> 3) * 8 + (j >> 3)) * 64 + (j & 7) * 8 + (k & 7));
-      const double parts[2] = {u.real(), u.imag()};
       for (int ri = 0; ri < 2; ++ri) {
-        double y = parts[ri] * 128.0;
         double scale = 1.0 / 128.0;  // digits at their true scale
         for (int q = 0; q < 3; ++q) {
-          const double d = std::nearbyint(y);
-          h[(size_t)(3 * ri + q) * m + w] = bf16_of_int(d, scale);
-          y = (y - d) * 256.0;
+          h[(size_t)(3 * ri + q) * m + w] = bf16_of(dg[3 * (2 * e + ri) + q], scale);
           scale /= 256.0;
         }
       }

@@ -1220,6 +1220,40 @@ int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
   return SV_OK;
 }
 
+int sv_host_pass_operand(int L, const sv_floquet_params* p, int n, int pass, int split,
+                         double* operand_out) {
+  if (!p || !operand_out) return SV_EINVAL;
+  if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  if (n < 2 || n > 7 || n > L) return SV_EINVAL;
+  if (split != SV_SPLIT_BF16X3 && split != SV_SPLIT_FP32) return SV_EINVAL;
+  if (split == SV_SPLIT_BF16X3 && n != 6) return SV_EINVAL;
+  auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
+  auto plan = fsv::fusion_plan(L, gates, n);
+  if (pass < 0 || pass >= (int)plan.size()) return SV_EINVAL;
+  const size_t dim = (size_t)1 << n;
+  const std::vector<fsv::cd>& U = plan[pass].U;
+  if (split == SV_SPLIT_FP32) {
+    std::vector<float2> f(dim * dim);
+    std::vector<float4> lead(dim);
+    fsv::round_unitary_fp32((int)dim, U.data(), f.data(), lead.data());
+    for (size_t e = 0; e < dim * dim; ++e) {
+      operand_out[2 * e] = f[e].x;
+      operand_out[2 * e + 1] = f[e].y;
+    }
+    for (size_t j = 0; j < dim; ++j) {  // the leading entries with their residuals
+      const size_t e = j * dim + (size_t)lead[j].z;
+      operand_out[2 * e] += lead[j].x;
+      operand_out[2 * e + 1] += lead[j].y;
+    }
+  } else {
+    std::vector<double> d(6 * dim * dim);
+    fsv::round_unitary_digits((int)dim, U.data(), d.data());
+    for (size_t e = 0; e < 2 * dim * dim; ++e)
+      operand_out[e] = (d[3 * e] + d[3 * e + 1] / 256.0 + d[3 * e + 2] / 65536.0) / 128.0;
+  }
+  return SV_OK;
+}
+
 int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes,
                          int* tile_a, int* sigma_out, unsigned char* rows_out,
                          int* store_wavefronts, int* x_sites_out,

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -52,6 +53,9 @@ struct PassArgs {
   int8_t ssig[13] = {};  // spos[sigma[k]]: staging bit of window / row bit k
   int8_t st_ndims = 3, st_tlo_dim = 1, st_tlo_shift = 2, st_thi_dim = 2, st_thi_shift = 7;
   const float2* U = nullptr; // fused unitary, FP32, row-major 2^n x 2^n
+  // per output row j: FP32 residual of its largest entry and that entry's
+  // column (re, im, column, 0); the CUDA-core pass starts row j's sum there
+  const float4* Ulead = nullptr;
   const void* W = nullptr;   // tensor-core operand block of this pass
   void* psi = nullptr;       // state (set at launch)
   double* partial = nullptr; // per-CTA (energy, norm) pairs or nullptr
@@ -65,6 +69,7 @@ struct BlockPlan {
   std::vector<BlockPass> passes;
   std::vector<PassArgs> args;
   float2* d_U = nullptr;
+  float4* d_Ulead = nullptr;
   void* d_W = nullptr;
   size_t w_bytes_per_pass = 0;
   double* d_partials = nullptr;
@@ -130,5 +135,20 @@ int block_tc_layout(PassArgs& pa);
 // -1 if the staging order needs more dimensions than a tensor map has.
 int block_tc_store_view(const PassArgs& pa, uint64_t* dims, uint64_t* strides, uint32_t* box);
 void block_tc_pack_w(int n, const std::vector<cd>& U, std::vector<uint32_t>& out);
+
+// Representable copies of a dim x dim unitary, as close to unitary as the
+// format allows (host_round.cpp): each real entry takes one of the two
+// values bracketing it, chosen by a coordinate descent on
+// ||Ur^H Ur - I||_F^2 + tr(Ur^H Ur - I)^2 from nearest rounding.
+//   FP32 entries (CUDA-core pass).  With lead != NULL, each row j's largest
+//   entry is stored to nearest and applied together with its FP32 residual
+//   lead[j] = (re, im, column, 0), so it counts as exact in the descent:
+void round_unitary_fp32(int dim, const cd* U, float2* out, float4* lead);
+//   tensor-core digits u = 2^-7 (u0 + u1/256 + u2/65536), u0 an integer and
+//   u1, u2 with 8 significant bits (u2 the chosen one): digits[3 (2 e + p) + t]
+//   is digit t of entry e's real (p = 0) or imaginary (p = 1) part.
+void round_unitary_digits(int dim, const cd* U, double* digits);
+// Run job(0..count-1) on up to 16 host threads.
+void round_passes_parallel(int count, const std::function<void(int)>& job);
 
 }  // namespace fsv

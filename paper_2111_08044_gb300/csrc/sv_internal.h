@@ -91,6 +91,10 @@ std::vector<AdjOp> adjoint_period_ops(int L, const sv_floquet_params &p, double 
 std::vector<Gate2> period_gates(int L, const sv_floquet_params &p, double theta,
                                 double hx);
 Observable observable(int L, const sv_floquet_params &p);
+// Share of the on-site fields (h_x, h_z) that site i carries in H0 = sum_b h_b:
+// 1/2 from each bond it belongs to, edge_field_weight from an open end's
+// single bond.  Allocates nothing.
+double site_field_share(int L, int i, double ew);
 bool params_valid(int L, const sv_floquet_params &p, std::string *why);
 
 // a3: fusion of one period into n-site block passes (host, FP64).

@@ -71,14 +71,6 @@ int setup_device(int dev, DeviceSymbols* out) {
   return SV_OK;
 }
 
-// share of the on-site fields held by site i (1 inside, edge weight at ends)
-double site_weight(int L, int i, double ew) {
-  double w = 0.0;
-  if (i >= 1) w += (i == L - 1) ? ew : 0.5;
-  if (i <= L - 2) w += (i == 0) ? ew : 0.5;
-  return w;
-}
-
 }  // namespace
 
 extern "C" int sv_energy_noalloc(const void* psi_dev, int L, int precision,
@@ -89,6 +81,10 @@ extern "C" int sv_energy_noalloc(const void* psi_dev, int L, int precision,
   const int lmax = precision == SV_C128 ? 33 : 34;
   if (L < 2 || L > lmax) return SV_EINVAL;  // beyond the scratch's size
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
+  // a general two-site chain's observable is sum_b H_b, which these
+  // Ising-form passes do not measure (sv_expect_energy sends such chains to
+  // the general-bond kernel)
+  if (p->h_bonds) return SV_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
@@ -124,15 +120,17 @@ extern "C" int sv_energy_noalloc(const void* psi_dev, int L, int precision,
     fsv::EpiParams ep;
     ep.flags = flags[k];
     const int b = bonds[k];
-    if (flags[k] & fsv::EPI_X_HI) ep.cx_hi = p->hx * site_weight(L, b, ew);
-    if (flags[k] & fsv::EPI_X_LO) ep.cx_lo = p->hx * site_weight(L, b + 1, ew);
+    if (flags[k] & fsv::EPI_X_HI) ep.cx_hi = p->hx * fsv::site_field_share(L, b, ew);
+    if (flags[k] & fsv::EPI_X_LO) ep.cx_lo = p->hx * fsv::site_field_share(L, b + 1, ew);
     if (flags[k] & fsv::EPI_DIAG) {
       ep.J = p->J;
-      ep.cz_first = p->hz * site_weight(L, 0, ew);
-      ep.cz_last = p->hz * site_weight(L, L - 1, ew);
-      ep.cz_bulk = L >= 3 ? p->hz * site_weight(L, 1, ew) : 0.0;
+      ep.cz_first = p->hz * fsv::site_field_share(L, 0, ew);
+      ep.cz_last = p->hz * fsv::site_field_share(L, L - 1, ew);
+      ep.cz_bulk = L >= 3 ? p->hz * fsv::site_field_share(L, 1, ew) : 0.0;
     }
     ep.partial = sym.scratch + (size_t)2 * kMaxBlocks * k;
+    // each pass writes one (energy, norm) pair per block into its slice
+    if (fsv::plain_gate_grid(L, b, precision, cfg) > kMaxBlocks) return SV_EINVAL;
     cudaError_t e = fsv::launch_plain_gate(precision, const_cast<void*>(psi_dev), L, b, ident,
                                            0, sym.counter, ep, /*store=*/0, cfg, s);
     if (e != cudaSuccess) return SV_ECUDA;

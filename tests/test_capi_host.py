@@ -102,7 +102,7 @@ def test_folded_period_equals_oracle_period(svlib, L, first):
     np.testing.assert_allclose(U @ orc.product_state(sp), psi, atol=1e-12, rtol=0)
 
 
-def _plan(svlib, L, n, **kw):
+def _plan(svlib, L, n, want_unitaries=False, **kw):
     p, keep = capi.make_params(**kw)
     cnt = ctypes.c_int(0)
     assert svlib.sv_host_fusion_plan(L, ctypes.byref(p), n, ctypes.byref(cnt), None, None,
@@ -111,7 +111,7 @@ def _plan(svlib, L, n, **kw):
     lo = np.zeros(P, dtype=np.int32)
     gc = np.zeros(P, dtype=np.int32)
     dim = 1 << n
-    U = np.zeros((P, dim, dim), dtype=np.complex128) if L <= 12 else None
+    U = np.zeros((P, dim, dim), dtype=np.complex128) if L <= 12 or want_unitaries else None
     assert svlib.sv_host_fusion_plan(
         L, ctypes.byref(p), n, ctypes.byref(cnt), lo.ctypes.data_as(capi._ip),
         gc.ctypes.data_as(capi._ip), None if U is None else U.ctypes.data_as(capi._dp)) == 0
@@ -135,6 +135,75 @@ def test_fused_passes_multiply_to_the_period(svlib, L, n):
     Ud = dr.floquet_dense([dr.ising_bond_dense(L, b, 1.0, 0.9, 0.4, 0.5) for b in range(L - 1)],
                           L, 0.125, 0.3, 4, 0)
     np.testing.assert_allclose(total, Ud, atol=1e-12, rtol=0)
+
+
+def _nearest_digits(x):
+    """The tensor-core digit value 2^-7 (u0 + u1/256 + u2/65536) with every
+    digit an integer rounded to nearest (the scheme before the descent)."""
+    y, out, sc = x * 128.0, np.zeros_like(x), 1.0 / 128.0
+    for _ in range(3):
+        d = np.rint(y)
+        out, y, sc = out + d * sc, (y - d) * 256.0, sc / 256.0
+    return out
+
+
+def _defect(M):
+    D = M.conj().T @ M - np.eye(M.shape[0])
+    return D, float(np.sum(np.abs(D) ** 2) + np.trace(D).real ** 2)
+
+
+@pytest.mark.parametrize("L", [14, 26])
+def test_pass_operands_are_close_to_unitary(svlib, L):
+    """Every block pass applies the same rounded copy of its fused unitary
+    each period, so a defect Ur^H Ur - I changes the norm by the same amount
+    every period.  The operands stay within the format's spacing of the FP64
+    unitary, their defect is no larger than nearest rounding's, and the trace
+    of the defect summed over the period's passes (the norm change per period
+    of a maximally mixed state) is far below nearest rounding's."""
+    n = 6
+    p, _ = capi.make_params(mode=capi.SV_MODE_BLOCK, block_n=n)
+    lo, gc, U = _plan(svlib, L, n, want_unitaries=True)
+    trace_sum = {capi.SV_SPLIT_BF16X3: 0.0, capi.SV_SPLIT_FP32: 0.0}
+    trace_near = dict(trace_sum)
+    for k in range(len(lo)):
+        for split in trace_sum:
+            o = np.zeros(2 * 4 ** n)
+            assert svlib.sv_host_pass_operand(L, ctypes.byref(p), n, k, split,
+                                              o.ctypes.data_as(capi._dp)) == 0
+            Ur = o.view(np.complex128).reshape(1 << n, 1 << n)
+            err = np.maximum(np.abs((Ur - U[k]).real), np.abs((Ur - U[k]).imag))
+            if split == capi.SV_SPLIT_BF16X3:
+                # u0 integer; u1, u2 8-bit significands; the chosen u2 is one
+                # of the two neighbours of its exact value: within 2^-25
+                assert err.max() <= 2.0 ** -25
+                Un = _nearest_digits(U[k].real) + 1j * _nearest_digits(U[k].imag)
+                # the digits are exact bf16 values: u0/128 a multiple of 2^-7
+                u0 = np.rint(U[k].real * 128.0)
+                assert np.all(np.abs(u0) <= 128)
+            else:
+                spacing = np.spacing(np.abs(U[k].astype(np.complex64).real).astype(np.float32))
+                assert np.all(np.abs((Ur - U[k]).real) <= spacing.astype(np.float64) * 1.0001)
+                # each row's largest entry is applied with its residual (exact
+                # to ~2^-48); every other entry is an FP32 value
+                lead = np.argmax(np.abs(U[k]), axis=1)
+                rows = np.arange(1 << n)
+                assert np.all(np.abs(Ur[rows, lead] - U[k][rows, lead]) < 1e-13)
+                rest = np.ones(Ur.shape, bool)
+                rest[rows, lead] = False
+                assert np.all(Ur.real[rest] == Ur.real[rest].astype(np.float32))
+                assert np.all(Ur.imag[rest] == Ur.imag[rest].astype(np.float32))
+                Un = U[k].astype(np.complex64).astype(np.complex128)
+            D, f = _defect(Ur)
+            Dn, fn = _defect(Un)
+            assert f <= fn * 1.000001
+            trace_sum[split] += np.trace(D).real / (1 << n)
+            trace_near[split] += np.trace(Dn).real / (1 << n)
+            if split == capi.SV_SPLIT_BF16X3:
+                # the 8-bit last digits leave a much smaller defect
+                assert np.linalg.norm(D) < 0.2 * np.linalg.norm(Dn)
+    for split in trace_sum:
+        assert abs(trace_sum[split]) < 2e-9, (split, trace_sum[split], trace_near[split])
+        assert abs(trace_sum[split]) < 0.1 * abs(trace_near[split])
 
 
 @pytest.mark.parametrize("L", [13, 20, 26, 30, 34])

@@ -28,7 +28,13 @@ if ROOT not in sys.path:
 METRIC = "Floquet periods/s at L=30 c64 (plain vs tensor-core block form), % of roofline"
 UNIT = "periods/s"
 L_BENCH = 30
-WORKLOAD = ("L=30 open chain, complex64 (8 GiB state), J=1 hx=0.9 hz=0.4 T=0.5 K=4 "
+
+
+def _workload(L: int) -> str:
+    size = 8 << L
+    human = (f"{size >> 30} GiB" if size >= 1 << 30 else
+             f"{size >> 20} MiB" if size >= 1 << 20 else f"{size >> 10} KiB")
+    return (f"L={L} open chain, complex64 ({human} state), J=1 hx=0.9 hz=0.4 T=0.5 K=4 "
             "theta=0.3, random product state (seed 4 + rank)")
 
 
@@ -38,6 +44,8 @@ def _parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="time the FP64 oracle at several chain lengths and thread counts")
     ap.add_argument("--L", type=int, default=L_BENCH)
     ap.add_argument("--n", type=int, default=6, help="block width of the fused form")
     ap.add_argument("--split", choices=["bf16x3", "fp32"], default="bf16x3")
@@ -261,60 +269,155 @@ def _batch(args, local):
     }
 
 
-def _oracle_periods_per_s(L_sample: int, periods: int, seed: int):
-    """FP64 oracle on the host cores: `periods` full periods at L_sample,
-    scaled to L=30 by amplitudes x two-qubit gates per period."""
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_full_periods(L: int, periods: int, seed: int, threads=None):
+    """The FP64 oracle on the host cores: `periods` full periods (gates, kick
+    and the energy / norm measurement of each period) of the bench circuit
+    at chain length L, timed as they stand.  Returns (periods/s, seconds,
+    threads used)."""
     from oracle import oracle as orc
     from paper_2111_08044_gb300 import inputs
-    cfg = inputs.ChainConfig(L=L_sample, seed=seed)
+    if threads is not None:
+        orc.set_threads(threads)
+    cfg = inputs.ChainConfig(L=L, seed=seed)
     psi = orc.product_state(cfg.spinors())
     hdrive, hobs = orc.chain_inputs(cfg)
     t0 = time.perf_counter()
     orc.evolve(psi, periods, hdrive, cfg.tau, cfg.theta, cfg.K, cfg.first_layer, hobs)
     dt = time.perf_counter() - t0
-    scale = ((1 << L_sample) * (L_sample - 1)) / ((1 << L_BENCH) * (L_BENCH - 1))
-    return periods / dt * scale, dt
+    used = orc.num_threads()
+    del psi
+    return periods / dt, dt, used
 
 
-# DRAM bytes (read + write) of one tensor-core block pass from an ncu
-# capture at L=26 (profiles/k_block_tc_L26.md), per launch; traffic scales
-# with the number of tiles, i.e. with 2^L.
-TC_TRAFFIC_L26 = 1012.8e6
+def _oracle_period_groups(L: int, seed: int):
+    """The FP64 oracle's period at chain length L cut into its 2K + 2
+    operation groups, in order: each gate layer (every bond of one parity,
+    index pairing), the kick (every site), and the energy / norm
+    measurement.  Any 2K + 2 consecutive groups do one whole period's work.
+    Returns (state, groups)."""
+    from oracle import oracle as orc
+    from paper_2111_08044_gb300 import inputs
+    cfg = inputs.ChainConfig(L=L, seed=seed)
+    psi = orc.product_state(cfg.spinors())
+    hdrive, hobs = orc.chain_inputs(cfg)
+    gates = orc.bond_gates(hdrive, cfg.tau)
+    kick = orc.kick_gates(L, cfg.theta)
+    groups = []
+    for _ in range(cfg.K):
+        for layer in range(2):
+            parity = cfg.first_layer if layer == 0 else 1 - cfg.first_layer
+
+            def gate_layer(parity=parity):
+                for b in range(parity, L - 1, 2):
+                    orc.apply_2q(psi, b, gates[b])
+            groups.append(gate_layer)
+
+    def kick_all():
+        for i in range(L):
+            orc.apply_1q(psi, i, kick[i])
+    groups.append(kick_all)
+
+    def measure():
+        orc.energy(psi, hobs)
+    groups.append(measure)
+    return psi, groups
+
+
+# DRAM bytes of one tensor-core block pass, read + write, per launch, from
+# an ncu capture of three launches at L = 28 (2 GiB state, 1024 tiles per
+# CTA): reads 2147.9 MB (the 2147.5 MB the pass must read), writes 2084.1 MB
+# (61 MB of the pass's output still sits in L2 when the kernel ends and is
+# written back during the next pass).  Traffic scales with the number of
+# tiles, i.e. with 2^L.
+TC_TRAFFIC_L28 = 2147.9e6 + 2084.1e6
 
 
 def _traffic(args):
-    if args.split != "bf16x3" or args.n != 6 or TC_TRAFFIC_L26 is None:
+    if args.split != "bf16x3" or args.n != 6:
         return None
-    return TC_TRAFFIC_L26 * 2.0 ** (args.L - 26)
-
-
-def _cpu_cores():
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return TC_TRAFFIC_L28 * 2.0 ** (args.L - 28)
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores, on this bench's config:
+    step k runs operation group k (mod 2K + 2) of the L=30 period, so 20
+    timed steps after 5 warm-up steps are exactly two whole periods."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
-    L_s = 24
-    vals = []
+    psi, groups = _oracle_period_groups(args.L, seed=_rank_seed(0))
+    ng = len(groups)
+    times = []
     for k in range(args.warmup + args.steps):
-        v, _ = _oracle_periods_per_s(L_s, 1, seed=4)
+        t0 = time.perf_counter()
+        groups[k % ng]()
+        dt = time.perf_counter() - t0
         if k >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
-    sample = (f"1 full period of the same circuit at L={L_s} per step (FP64 oracle, "
-              f"index pairing), scaled to L=30 by 2^L x (L-1)")
+            times.append(dt)
+    from oracle import oracle as orc
+    total = sum(times)
+    value = (args.steps / ng) / total
+    sample = (f"the FP64 oracle (index pairing, OpenMP) at L={args.L}: step k is operation "
+              f"group k mod {ng} of the period (8 gate layers, the kick, the energy and norm "
+              f"measurement); the {args.steps} timed steps do {args.steps / ng:g} periods' "
+              f"work (exactly whole periods when steps is a multiple of {ng}); "
+              f"CPU: {_cpu_model()}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "form": "FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
-                         "sample": sample},
+        "data": "synthetic", "config": _config(args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.num_threads(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    del psi
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, world):
+    l2 = (f"inputs exceed L2 ({(8 << args.L) >> 20} MiB state per replica); no flush" if (8 << args.L) > (129 << 20)
+          else "state fits in L2: not the bench workload")
+    return {"workload": _workload(args.L),
+            "form": f"block n={args.n} {args.split}",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": l2}
+
+
+def run_oracle_table(args):
+    """The oracle's CPU-baseline table: whole periods at several chain
+    lengths, all cores and one thread (one JSON line per entry)."""
+    from oracle import oracle as orc
+    allc = orc.num_threads()
+    plan = [(12, 100, allc), (12, 100, 1), (20, 100, allc), (20, 100, 1), (26, 10, allc),
+            (26, 1, 1), (30, 2, allc)]
+    for L, periods, th in plan:
+        v, dt, used = _oracle_full_periods(L, periods, seed=4, threads=th)
+        print(json.dumps({"oracle_table": True, "L": L, "periods": periods, "threads": used,
+                          "seconds": dt, "periods_per_s": v,
+                          "two_qubit_gates_per_s": v * 4 * (L - 1), "cpu": _cpu_model()}),
+              flush=True)
+    orc.set_threads(allc)
     return 0
 
 
@@ -347,10 +450,10 @@ def run_ours(args):
     batch = _batch(args, local) if args.batch_periods > 0 else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt = _oracle_periods_per_s(24, 2, seed=4)
-        cpu = {"value": v, "unit": UNIT, "cores": _cpu_cores(), "kind": "oracle",
-               "sample": f"2 full periods at L=24 ({dt:.1f} s, FP64 oracle), scaled to L=30 "
-                         "by 2^L x (L-1)"}
+        v, dt, used = _oracle_full_periods(args.L, 1, seed=_rank_seed(0))
+        cpu = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": f"one whole period (gates, kick, energy and norm) of this workload at "
+                         f"L={args.L} in FP64 ({dt:.1f} s), no scaling; CPU: {_cpu_model()}"}
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -364,9 +467,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (complex64 state; block GEMMs "
         + ("tensor cores on exact bf16 digits, FP32 accumulators" if args.split == "bf16x3" else "FP32") + ", FP64 reductions)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": f"block n={args.n} {args.split}",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "inputs exceed L2 (8 GiB state per replica); no flush"},
+        "config": _config(args, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": _traffic(args),
                      "kernel": "block pass (one fused unitary + relabel per launch)",
@@ -392,6 +493,8 @@ def run_ours(args):
 
 def main():
     args = _parse()
+    if args.oracle_table:
+        return run_oracle_table(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

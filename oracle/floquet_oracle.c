@@ -43,6 +43,22 @@ typedef double complex cplx;
 
 int or_version(void) { return 1; }
 
+/* Thread count of the OpenMP loops (for the timed CPU baseline: single-
+ * thread and all-core runs in one process).  No arithmetic depends on it
+ * beyond the order of the parallel reductions' partial sums. */
+#ifdef _OPENMP
+#include <omp.h>
+int or_max_threads(void) { return omp_get_max_threads(); }
+int or_set_threads(int n) {
+  if (n < 1) return OR_EINVAL;
+  omp_set_num_threads(n);
+  return OR_OK;
+}
+#else
+int or_max_threads(void) { return 1; }
+int or_set_threads(int n) { return n < 1 ? OR_EINVAL : OR_OK; }
+#endif
+
 /* ---------------------------------------------------------------- matrices */
 
 static void mat_load(int n, const double *src, cplx *dst) {

@@ -62,7 +62,7 @@ def test_reference_arm_two_ranks():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--L", "16"]
     env = dict(os.environ, OMP_NUM_THREADS="2")
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -71,3 +71,25 @@ def test_reference_arm_two_ranks():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_groups_make_one_period():
+    """The reference arm's steps are the period's operation groups; the
+    2K + 2 groups in order do exactly the oracle's whole period."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as orc
+    from paper_2111_08044_gb300 import inputs
+    L = 10
+    psi, groups = bench._oracle_period_groups(L, seed=4)
+    cfg = inputs.ChainConfig(L=L, seed=4)
+    assert len(groups) == 2 * cfg.K + 2
+    ref = orc.product_state(cfg.spinors())
+    hdrive, hobs = orc.chain_inputs(cfg)
+    for _ in range(2):
+        for g in groups:
+            g()
+        orc.period(ref, orc.bond_gates(hdrive, cfg.tau), orc.kick_gates(L, cfg.theta), cfg.K,
+                   cfg.first_layer)
+    np.testing.assert_allclose(psi, ref, atol=1e-14, rtol=0)

@@ -9,8 +9,13 @@
 // every pending gate inside its window whose predecessors are done.  Moving
 // the window by more than 7 sites costs extra relabel-only passes (the
 // state layout changes through a 7-bit row index), as does returning to the
-// first window (site 0) at the end of the period, because every period
-// starts from the natural layout.
+// period's first window at the end of the period, because every period
+// starts from the same layout.  That first window sits at site 0 (the
+// natural layout), or, for a cyclic plan, at the start s <= 7 that needs
+// the fewest passes: the state then stays in the layout of window s from
+// one period to the next, and a single relabel pass at the start of an
+// evolution (and the last period's last pass writing the natural layout)
+// take it there and back.
 #include <algorithm>
 #include <cstdint>
 #include <map>
@@ -109,7 +114,7 @@ using Hist = std::vector<std::pair<int, std::vector<int>>>;  // (lo or -1, gates
 // merged in the order a single thread would produce them, so the plan does
 // not depend on the thread count.  States link to their parents; the
 // sequence of passes is read back once at the end.
-Hist plan_search(const Dag& dag, int L, int n, int ng) {
+Hist plan_search(const Dag& dag, int L, int n, int ng, int start) {
   const int words = (ng + 63) / 64;
   const size_t beam = ng <= 200 ? 256 : 32;
   // levels[k]: states after k passes (relabel-only passes included)
@@ -120,7 +125,7 @@ Hist plan_search(const Dag& dag, int L, int n, int ng) {
   levels[0].push_back(s0);
   int best_total = 1 << 30;
   State best;
-  int best_tail = 0;  // relabel-only passes back to site 0 after the last window
+  int best_tail = 0;  // relabel-only passes back to the start after the last window
   struct Cand {
     State t;
     int kk;
@@ -144,8 +149,9 @@ Hist plan_search(const Dag& dag, int L, int n, int ng) {
     auto expand = [&](size_t i0, size_t i1) {
       for (size_t i = i0; i < i1; ++i) {
         const State& s = kept[i];
-        const int lo_max = s.lo < 0 ? 0 : L - n;  // the first window starts at site 0
-        for (int lo = 0; lo <= lo_max; ++lo) {
+        // the first window is the period's start
+        const int lo_min = s.lo < 0 ? start : 0, lo_max = s.lo < 0 ? start : L - n;
+        for (int lo = lo_min; lo <= lo_max; ++lo) {
           State t;
           t.done = s.done;
           t.ab = absorb(dag, t.done, lo, n);
@@ -173,11 +179,11 @@ Hist plan_search(const Dag& dag, int L, int n, int ng) {
     for (auto& cs : per)
       for (Cand& c : cs) {
         if (c.t.count == ng) {
-          const int total = c.kk + shift_cost(c.t.lo, 0);
+          const int total = c.kk + shift_cost(c.t.lo, start);
           if (total < best_total) {
             best_total = total;
             best = c.t;
-            best_tail = shift_cost(c.t.lo, 0);
+            best_tail = shift_cost(c.t.lo, start);
           }
           continue;
         }
@@ -197,19 +203,32 @@ Hist plan_search(const Dag& dag, int L, int n, int ng) {
   return Hist(rev.rbegin(), rev.rend());
 }
 
+// The plan from the best start: site 0 only, or (cyclic) every start
+// s <= 7 (a single relabel pass then reaches it from the natural layout),
+// the fewest passes winning and the smaller start breaking ties.
+Hist best_plan(const Dag& dag, int L, int n, int ng, bool cyclic) {
+  Hist best = plan_search(dag, L, n, ng, 0);
+  const int smax = cyclic ? std::min(kMaxShift, L - n) : 0;
+  for (int s = 1; s <= smax; ++s) {
+    Hist h = plan_search(dag, L, n, ng, s);
+    if (h.size() < best.size()) best.swap(h);
+  }
+  return best;
+}
+
 // Plans depend only on the gate structure (bond sequence, L, n), not on the
 // gate values: a rebuild with new parameters reuses the search.
-Hist cached_plan(const Dag& dag, int L, int n, int ng) {
+Hist cached_plan(const Dag& dag, int L, int n, int ng, bool cyclic) {
   static std::mutex mu;
   static std::map<std::vector<int>, Hist> cache;
-  std::vector<int> key{L, n};
+  std::vector<int> key{L, n, cyclic ? 1 : 0};
   key.insert(key.end(), dag.bond.begin(), dag.bond.end());
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
-  Hist h = plan_search(dag, L, n, ng);
+  Hist h = best_plan(dag, L, n, ng, cyclic);
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() >= 64) cache.clear();
   cache.emplace(std::move(key), h);
@@ -218,10 +237,16 @@ Hist cached_plan(const Dag& dag, int L, int n, int ng) {
 
 }  // namespace
 
-std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n) {
+std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n, bool cyclic) {
   const Dag dag = make_dag(gates, L);
   const int ng = (int)gates.size();
-  const Hist hist = cached_plan(dag, L, n, ng);
+  const Hist hist = cached_plan(dag, L, n, ng, cyclic);
+  int start = 0;
+  for (const auto& h : hist)
+    if (h.first >= 0) {
+      start = h.first;
+      break;
+    }
   // Materialise passes: fused unitaries, energy flags.  A relabel-only pass
   // keeps an identity unitary on a window that steps toward the next one.
   std::vector<BlockPass> out;
@@ -231,7 +256,7 @@ std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n
     last_gate[gates[k].bond] = k;
     last_gate[gates[k].bond + 1] = k;
   }
-  int prev_lo = 0;
+  int prev_lo = start;
   for (size_t h = 0; h < hist.size(); ++h) {
     BlockPass p;
     p.n = n;
@@ -239,8 +264,8 @@ std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n
       p.lo = hist[h].first;
       p.gates = hist[h].second;
     } else {
-      // find the next real window (or site 0 at the end) and step toward it
-      int target = 0;
+      // find the next real window (or the start at the end) and step toward it
+      int target = start;
       for (size_t q = h + 1; q < hist.size(); ++q)
         if (hist[q].first >= 0) {
           target = hist[q].first;

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kSimtThreads) k_block_simt(float2* __restrict_
       if (pa.diag) {
         const float p = cabs2(v);
         ns += p;
-        es += p * dg(x);
+        es += p * dg(to_natural(x, N, pa.diag_lo));
       }
     }
     eacc += (double)es;
@@ -169,6 +169,9 @@ cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStrea
   }
 }
 
+// a pass's relabel moves the window by at most its 7 row bits
+constexpr int kMaxShiftRows = 7;
+
 std::string block_tile_layout(int L, int n, int R, int lo, int lo_next, int* a_out,
                               int8_t* sigma) {
   const int lo_min = std::min(lo, lo_next);
@@ -196,7 +199,8 @@ std::string block_tile_layout(int L, int n, int R, int lo, int lo_next, int* a_o
 }
 
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
-                int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg) {
+                int split, const LaunchCfg& cfg, bool cyclic, BlockPlan** out,
+                std::string* msg) {
   *out = nullptr;
   if (split != SV_SPLIT_BF16X3 && split != SV_SPLIT_FP32) {
     *msg = "unknown split";
@@ -208,8 +212,9 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   bp->R = std::min(7, L - n);
   bp->split = split;
   bp->cfg = cfg;
-  bp->passes = fusion_plan(L, gates, n);
+  bp->passes = fusion_plan(L, gates, n, cyclic);
   const int P = (int)bp->passes.size();
+  bp->start = bp->passes[0].lo;
   const int R = bp->R;
   bp->tensor_cores = split == SV_SPLIT_BF16X3 && block_tc_supported(L, n);
   const long long ntiles = 1ll << (L - n - R);
@@ -223,11 +228,56 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     block_free(bp);
     return SV_EINVAL;
   };
+  // The launches: the period's P passes, each writing the next pass's layout
+  // (the last one the start's); when the start is not site 0, the last
+  // period of an evolution ends with a variant of the last pass that writes
+  // toward the natural layout (plus relabel steps if it is more than 7 sites
+  // away), and an evolution begins with relabel steps from the natural
+  // layout to the start.  A relabel step applies the identity.
+  struct Op {
+    int src;  // pass whose unitary and measurements it applies, -1: identity
+    int lo, lo_next;
+  };
+  std::vector<Op> ops;
+  for (int k = 0; k < P; ++k) ops.push_back({k, bp->passes[k].lo, bp->passes[(k + 1) % P].lo});
+  auto step = [](int from, int to) {
+    return from + std::max(-kMaxShiftRows, std::min(kMaxShiftRows, to - from));
+  };
+  for (int k = 0; k < P; ++k) bp->seq_cyc.push_back(k);
+  if (bp->start == 0) {
+    bp->seq_exit = bp->seq_cyc;
+  } else {
+    for (int k = 0; k + 1 < P; ++k) bp->seq_exit.push_back(k);
+    int lo = bp->passes[P - 1].lo, nx = step(lo, 0);
+    bp->seq_exit.push_back((int)ops.size());
+    ops.push_back({P - 1, lo, nx});
+    while (nx != 0) {
+      lo = nx;
+      nx = step(lo, 0);
+      bp->seq_exit.push_back((int)ops.size());
+      ops.push_back({-1, lo, nx});
+    }
+    lo = 0;
+    while (lo != bp->start) {
+      nx = step(lo, bp->start);
+      bp->seq_entry.push_back((int)ops.size());
+      ops.push_back({-1, lo, nx});
+      lo = nx;
+    }
+  }
+  const BlockPass identity_pass = [&]() {
+    BlockPass ip;
+    ip.n = n;
+    ip.U.assign((size_t)1 << (2 * n), cd(0.0, 0.0));
+    for (size_t e = 0; e < ((size_t)1 << n); ++e) ip.U[e * ((size_t)1 << n) + e] = 1.0;
+    return ip;
+  }();
+  std::vector<int> slot_of(P, -1);
   int slot = 0;
-  for (int k = 0; k < P; ++k) {
-    const BlockPass& ps = bp->passes[k];
-    const int lo = ps.lo;
-    const int lo_next = bp->passes[(k + 1) % P].lo;
+  for (size_t k = 0; k < ops.size(); ++k) {
+    const BlockPass& ps = ops[k].src >= 0 ? bp->passes[ops[k].src] : identity_pass;
+    const int lo = ops[k].lo;
+    const int lo_next = ops[k].lo_next;
     PassArgs pa;
     pa.L = L;
     pa.n = n;
@@ -245,7 +295,7 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     }
     pa.diag = ps.diag && !obs.general ? 1 : 0;
     if (pa.diag) {
-      if (lo_next != 0) return fail("last pass must hand back the natural layout");
+      pa.diag_lo = lo_next;  // the output's layout (natural order: window at 0)
       pa.ep.flags = EPI_DIAG;
       pa.ep.J = obs.J;
       pa.ep.cz_first = obs.cz[0];
@@ -256,11 +306,10 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
       pa.diag_f[2] = (float)pa.ep.cz_first;
       pa.diag_f[3] = (float)pa.ep.cz_last;
       pa.diag_f[4] = (float)(pa.ep.cz_bulk * (L - 2) + pa.ep.cz_first + pa.ep.cz_last);
-      // per window bit: its site in the (natural) output, its field, and
-      // which of its neighbours lie outside the window
+      // per window bit: its site (window bit j is site lo + j in every
+      // layout), its field, and which of its neighbours lie outside the window
       int site[8];
-      for (int j = 0; j < n; ++j)
-        site[j] = pa.sigma[j] < n ? pa.sigma[j] : pa.a + pa.sigma[j] - n;
+      for (int j = 0; j < n; ++j) site[j] = lo + j;
       for (int j = 0; j < n; ++j) {
         const int g = site[j];
         const double czg = g == 0 ? pa.ep.cz_first : (g == L - 1 ? pa.ep.cz_last : pa.ep.cz_bulk);
@@ -277,20 +326,42 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
         pa.diag_lin0[j] = (float)(-2.0 * (czg + pa.ep.J * inside));
       }
     }
-    if (pa.x_mask || pa.diag) pa.slot = slot++;
+    if (pa.x_mask || pa.diag) {
+      // the exit variant of the last pass fills that pass's partials slot
+      if (ops[k].src >= 0 && slot_of[ops[k].src] >= 0) pa.slot = slot_of[ops[k].src];
+      else pa.slot = slot++;
+      if (ops[k].src >= 0) slot_of[ops[k].src] = pa.slot;
+    }
     bp->args.push_back(pa);
   }
+  const int NA = (int)bp->args.size();
   bp->nslots = slot;
   // device buffers
   const size_t dim = (size_t)1 << n;
-  std::vector<float2> hu(bp->tensor_cores ? 0 : (size_t)P * dim * dim);
-  std::vector<float4> hl(bp->tensor_cores ? 0 : (size_t)P * dim);
-  std::vector<std::vector<uint32_t>> hw(bp->tensor_cores ? P : 0);
-  // the operands of every pass, rounded close to unitary (host_round.cpp)
-  round_passes_parallel(P, [&](int k) {
-    if (bp->tensor_cores) block_tc_pack_w(n, bp->passes[k].U, hw[k]);
-    else round_unitary_fp32((int)dim, bp->passes[k].U.data(), &hu[k * dim * dim], &hl[k * dim]);
+  // the operands of the P passes and of the identity (index P), rounded
+  // close to unitary (host_round.cpp); every launch takes its source's copy
+  const int NU = P + 1;
+  std::vector<float2> uu(bp->tensor_cores ? 0 : (size_t)NU * dim * dim);
+  std::vector<float4> ul(bp->tensor_cores ? 0 : (size_t)NU * dim);
+  std::vector<std::vector<uint32_t>> uw(bp->tensor_cores ? NU : 0);
+  round_passes_parallel(NU, [&](int k) {
+    const std::vector<cd>& U = k < P ? bp->passes[k].U : identity_pass.U;
+    if (bp->tensor_cores) block_tc_pack_w(n, U, uw[k]);
+    else round_unitary_fp32((int)dim, U.data(), &uu[k * dim * dim], &ul[k * dim]);
   });
+  std::vector<float2> hu(bp->tensor_cores ? 0 : (size_t)NA * dim * dim);
+  std::vector<float4> hl(bp->tensor_cores ? 0 : (size_t)NA * dim);
+  std::vector<std::vector<uint32_t>> hw(bp->tensor_cores ? NA : 0);
+  for (int k = 0; k < NA; ++k) {
+    const int from = ops[k].src >= 0 ? ops[k].src : P;
+    if (bp->tensor_cores) {
+      hw[k] = uw[from];
+    } else {
+      std::copy(uu.begin() + from * dim * dim, uu.begin() + (from + 1) * dim * dim,
+                hu.begin() + k * dim * dim);
+      std::copy(ul.begin() + from * dim, ul.begin() + (from + 1) * dim, hl.begin() + k * dim);
+    }
+  }
   if (!bp->tensor_cores &&
       (cudaMalloc(&bp->d_U, sizeof(float2) * hu.size()) != cudaSuccess ||
        cudaMemcpy(bp->d_U, hu.data(), sizeof(float2) * hu.size(), cudaMemcpyHostToDevice) !=
@@ -306,7 +377,7 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
   if (bp->tensor_cores) {
     bp->w_bytes_per_pass = block_tc_w_bytes(n);
     std::vector<uint32_t> all;
-    for (int k = 0; k < P; ++k) all.insert(all.end(), hw[k].begin(), hw[k].end());
+    for (int k = 0; k < NA; ++k) all.insert(all.end(), hw[k].begin(), hw[k].end());
     if (cudaMalloc(&bp->d_W, all.size() * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemcpy(bp->d_W, all.data(), all.size() * sizeof(uint32_t),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -324,7 +395,7 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
     block_free(bp);
     return SV_ENOMEM;
   }
-  for (int k = 0; k < P; ++k) {
+  for (int k = 0; k < NA; ++k) {
     PassArgs& pa = bp->args[k];
     if (bp->d_U) {
       pa.U = bp->d_U + (size_t)k * dim * dim;
@@ -363,7 +434,7 @@ void block_info(const BlockPlan* bp, int* passes, int* launches) {
 }
 
 size_t block_upload_bytes(const BlockPlan* bp) {
-  const size_t P = bp->passes.size();
+  const size_t P = bp->args.size();
   const size_t dim = (size_t)1 << bp->n;
   const size_t u = bp->tensor_cores ? 0 : sizeof(float2) * dim * dim + sizeof(float4) * dim;
   return P * (u + bp->w_bytes_per_pass);
@@ -401,11 +472,21 @@ int block_status(BlockPlan* bp, cudaStream_t s) {
   return h;
 }
 
-cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
-                                 int ring_len, cudaStream_t s) {
+cudaError_t block_enqueue_entry(BlockPlan* bp, void* psi, cudaStream_t s) {
   cudaError_t e = ensure_maps(bp, psi);
   if (e != cudaSuccess) return e;
-  for (size_t k = 0; k < bp->args.size(); ++k) {
+  for (int k : bp->seq_entry) {
+    e = launch_pass(bp, k, psi, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
+                                 int ring_len, cudaStream_t s, bool last) {
+  cudaError_t e = ensure_maps(bp, psi);
+  if (e != cudaSuccess) return e;
+  for (int k : last ? bp->seq_exit : bp->seq_cyc) {
     e = launch_pass(bp, k, psi, s);
     if (e != cudaSuccess) return e;
   }
@@ -415,22 +496,27 @@ cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, d
 
 cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* counter,
                                         double* ring, int ring_len, cudaStream_t s,
-                                        cudaEvent_t* ev) {
+                                        cudaEvent_t* ev, bool last) {
   cudaError_t e = ensure_maps(bp, psi);
   if (e != cudaSuccess) return e;
-  size_t k = 0;
-  for (; k < bp->args.size(); ++k) {
-    e = cudaEventRecord(ev[k], s);
-    if (e != cudaSuccess) return e;
-    e = launch_pass(bp, k, psi, s);
+  // events around the period's P passes (the exit variant's relabel steps,
+  // if any, fall inside the last pass's interval) and the reduce
+  const std::vector<int>& seq = last ? bp->seq_exit : bp->seq_cyc;
+  const size_t P = bp->seq_cyc.size();
+  for (size_t k = 0; k < seq.size(); ++k) {
+    if (k < P) {
+      e = cudaEventRecord(ev[k], s);
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_pass(bp, (size_t)seq[k], psi, s);
     if (e != cudaSuccess) return e;
   }
-  e = cudaEventRecord(ev[k++], s);
+  e = cudaEventRecord(ev[P], s);
   if (e != cudaSuccess) return e;
   e = launch_period_reduce(bp->d_partials, (long long)bp->nslots * bp->maxb, bp->L, ring,
                            ring_len, counter, 1, s);
   if (e != cudaSuccess) return e;
-  return cudaEventRecord(ev[k], s);
+  return cudaEventRecord(ev[P + 1], s);
 }
 
 void block_free(BlockPlan* bp) {

@@ -572,8 +572,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int j = 0; j < kN; ++j) col_off[j] = swz128(8u << pa.ssig[j]);
     const uint32_t out_base = sbase + kOffOut;
-    // Diagonal part on the natural layout (the period's last pass), per
-    // amplitude h(x) = J sum_p z_p z_{p+1} + sum_p cz_p z_p, z = 1 - 2 x_p.
+    // Diagonal part of the period's last pass, per amplitude (x its natural
+    // index) h(x) = J sum_p z_p z_{p+1} + sum_p cz_p z_p, z = 1 - 2 x_p.
     // Within a row only the output bits fed by window bits change with c:
     // h(x_c) = h(x_0) + sum_j c_j lin_j + Q[c], where lin_j is the change of
     // flipping window bit j alone (its field and its bonds to the fixed
@@ -582,15 +582,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* diag_q = reinterpret_cast<float*>(misc + kDiagQ);
     const bool do_x = kGeneric ? pa.x_mask != 0 : kX;
     const bool do_diag = kGeneric ? pa.diag != 0 : kDiag;
-    // global bit of window bit j in the output
-    auto gcol = [&](int j) { return pa.sigma[j] < kN ? pa.sigma[j] : a + pa.sigma[j] - kN; };
     if (do_diag) {
       if (r < kCols) {
+        // window bits j and k are sites lo + j and lo + k: adjacent when
+        // |j - k| = 1
         float qv = 0.f;
-        for (int j = 0; j < kN; ++j)
-          for (int k = j + 1; k < kN; ++k)
-            if (((r >> j) & 1) && ((r >> k) & 1) && (gcol(j) - gcol(k) == 1 || gcol(k) - gcol(j) == 1))
-              qv += 4.f * (float)pa.ep.J;
+        for (int j = 0; j + 1 < kN; ++j)
+          if (((r >> j) & 1) && ((r >> (j + 1)) & 1)) qv += 4.f * (float)pa.ep.J;
         diag_q[r] = qv;
       }
       epilogue_sync();
@@ -666,10 +664,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tlo = (uint32_t)(t & ((1ll << (a - kN)) - 1));
       const uint32_t thi = (uint32_t)(t >> (a - kN));
       if (do_diag) {
-        // the period's last pass writes the natural layout: measure the
-        // diagonal part and the norm on the amplitudes' natural indices
+        // the diagonal part and the norm on the amplitudes' natural indices:
+        // x0, the row's amplitude at c = 0, mapped from the output's layout
         const uint64_t tbase = ((uint64_t)tlo << kN) | ((uint64_t)thi << (a + 7));
-        const uint64_t x0 = tbase | (yrow & (kCols - 1)) | ((uint64_t)(yrow >> kN) << a);
+        const uint64_t x0 = to_natural(
+            tbase | (yrow & (kCols - 1)) | ((uint64_t)(yrow >> kN) << a), kN, pa.diag_lo);
         // FP32 coefficients rounded on the host (no FP64 work per tile)
         Diag<float> dg;
         dg.L = pa.L;

@@ -60,7 +60,10 @@ struct sv_ctx {
   long long* d_counter = nullptr;
   fsv::BlockPlan* block = nullptr;  // block-mode plan and buffers
 
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;       // one period
+  cudaGraphExec_t graph_exit = nullptr;  // an evolution's last period (block plans
+                                         // whose periods start off site 0)
+  bool cyclic = true;  // block plans may start their periods off site 0
 
   int launches_per_period = 0;
   int passes_per_period = 0;
@@ -110,6 +113,17 @@ void drop_graph(sv_ctx* ctx) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
   }
+  if (ctx->graph_exit) {
+    cudaGraphExecDestroy(ctx->graph_exit);
+    ctx->graph_exit = nullptr;
+  }
+}
+
+// Block plans whose periods start at a window off site 0 keep the state in
+// that window's layout between periods: an evolution begins with relabel
+// steps into it and its last period hands back the natural layout.
+bool off_natural(const sv_ctx* ctx) {
+  return ctx->params.mode == SV_MODE_BLOCK && ctx->block && ctx->block->start != 0;
 }
 
 void free_build(sv_ctx* ctx) {
@@ -177,33 +191,57 @@ int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
   return SV_OK;
 }
 
-int enqueue_period(sv_ctx* ctx, cudaStream_t s) {
+int enqueue_period(sv_ctx* ctx, cudaStream_t s, bool last = false) {
   if (ctx->params.mode == SV_MODE_BLOCK) {
     cudaError_t e = fsv::block_enqueue_period(ctx->block, ctx->state, ctx->d_counter,
-                                              ctx->d_ring, kRing, s);
+                                              ctx->d_ring, kRing, s, last);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "block period launch");
     return SV_OK;
   }
   return enqueue_plain_period(ctx, s);
 }
 
-int ensure_graph(sv_ctx* ctx) {
-  if (ctx->graph) return SV_OK;
+int capture_period(sv_ctx* ctx, bool last, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   SV_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed),
           "begin capture");
-  int rc = enqueue_period(ctx, ctx->cap_stream);
+  int rc = enqueue_period(ctx, ctx->cap_stream, last);
   cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
   if (rc != SV_OK) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
-  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    ctx->graph = nullptr;
+    *out = nullptr;
     return cuda_fail(ctx, e, "graph instantiate");
+  }
+  return SV_OK;
+}
+
+int ensure_graph(sv_ctx* ctx) {
+  if (!ctx->graph) {
+    int rc = capture_period(ctx, false, &ctx->graph);
+    if (rc) return rc;
+  }
+  if (off_natural(ctx) && !ctx->graph_exit) return capture_period(ctx, true, &ctx->graph_exit);
+  return SV_OK;
+}
+
+// Launch `count` periods, the first of an evolution when `first` (preceded
+// by the relabel steps into the period layout) and its last when `last`.
+int launch_periods(sv_ctx* ctx, int64_t count, bool first, bool last) {
+  const bool off = off_natural(ctx);
+  if (first && off && count > 0) {
+    cudaError_t e = fsv::block_enqueue_entry(ctx->block, ctx->state, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "relabel launch");
+  }
+  for (int64_t k = 0; k < count; ++k) {
+    const bool exit = off && last && k + 1 == count;
+    SV_CUDA(cudaGraphLaunch(exit ? ctx->graph_exit : ctx->graph, ctx->stream), "graph launch");
+    ++ctx->counter;
   }
   return SV_OK;
 }
@@ -236,6 +274,8 @@ int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out) {
 void ctx_advance(sv_ctx* ctx, int64_t periods) { ctx->counter += periods; }
 
 void ctx_set_min_tiles(sv_ctx* ctx, int tiles) { ctx->cfg.min_tiles_per_cta = tiles; }
+
+void ctx_set_cyclic(sv_ctx* ctx, bool cyclic) { ctx->cyclic = cyclic; }
 
 int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n) {
   return read_ring(ctx, c0, count, e, n);
@@ -507,10 +547,10 @@ int product_overlap(sv_ctx* ctx, int group, const double* factors, double* overl
 }
 
 // One period with an event recorded before each launch and after the last.
-int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
+int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev, bool last) {
   if (ctx->params.mode == SV_MODE_BLOCK) {
     cudaError_t e = fsv::block_enqueue_period_events(ctx->block, ctx->state, ctx->d_counter,
-                                                     ctx->d_ring, kRing, s, ev);
+                                                     ctx->d_ring, kRing, s, ev, last);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "block period launch");
     return SV_OK;
   }
@@ -717,7 +757,7 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
     if (n > ctx->L) n = ctx->L;
     std::string msg;
     int rc = fsv::block_build(ctx->L, ctx->gates, ctx->obs, n, p->split, ctx->cfg,
-                              &ctx->block, &msg);
+                              ctx->cyclic, &ctx->block, &msg);
     if (rc != SV_OK) return fail(ctx, rc, "block build: %s", msg.c_str());
     fsv::block_set_renorm(ctx->block, renorm_of(ctx));
     fsv::block_info(ctx->block, &ctx->passes_per_period, &ctx->launches_per_period);
@@ -786,10 +826,8 @@ int sv_evolve(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out
   while (done < periods) {
     const int64_t chunk = std::min<int64_t>(periods - done, kRing);
     const int64_t c0 = ctx->counter;
-    for (int64_t k = 0; k < chunk; ++k) {
-      SV_CUDA(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
-      ++ctx->counter;
-    }
+    rc = launch_periods(ctx, chunk, done == 0, done + chunk == periods);
+    if (rc) return rc;
     if (energy_out || norm_out) {
       rc = read_ring(ctx, c0, chunk, energy_out ? energy_out + done : nullptr,
                      norm_out ? norm_out + done : nullptr);
@@ -820,8 +858,12 @@ int sv_evolve_profiled(sv_ctx* ctx, int64_t periods, double* energy_out, double*
     }
   const int64_t c0 = ctx->counter;
   rc = SV_OK;
+  if (periods > 0 && off_natural(ctx)) {
+    cudaError_t e = fsv::block_enqueue_entry(ctx->block, ctx->state, ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "relabel launch");
+  }
   for (int64_t p = 0; p < periods && rc == SV_OK; ++p) {
-    rc = enqueue_period_profiled(ctx, ctx->stream, ev.data());
+    rc = enqueue_period_profiled(ctx, ctx->stream, ev.data(), p + 1 == periods);
     if (rc) break;
     ++ctx->counter;
     if (rc == SV_OK) {
@@ -1202,7 +1244,7 @@ int sv_host_fusion_plan(int L, const sv_floquet_params* p, int n, int* n_passes,
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
   if (n < 2 || n > 7 || n > L) return SV_EINVAL;
   auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
-  auto plan = fsv::fusion_plan(L, gates, n);
+  auto plan = fsv::fusion_plan(L, gates, n, true);
   const int cap = *n_passes;
   *n_passes = (int)plan.size();
   if (!window_lo && !gate_count && !unitaries_out) return SV_OK;
@@ -1228,7 +1270,7 @@ int sv_host_pass_operand(int L, const sv_floquet_params* p, int n, int pass, int
   if (split != SV_SPLIT_BF16X3 && split != SV_SPLIT_FP32) return SV_EINVAL;
   if (split == SV_SPLIT_BF16X3 && n != 6) return SV_EINVAL;
   auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
-  auto plan = fsv::fusion_plan(L, gates, n);
+  auto plan = fsv::fusion_plan(L, gates, n, true);
   if (pass < 0 || pass >= (int)plan.size()) return SV_EINVAL;
   const size_t dim = (size_t)1 << n;
   const std::vector<fsv::cd>& U = plan[pass].U;
@@ -1262,7 +1304,7 @@ int sv_host_block_layout(int L, const sv_floquet_params* p, int n, int* n_passes
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
   if (n < 2 || n > 7 || n >= L) return SV_EINVAL;
   auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
-  auto plan = fsv::fusion_plan(L, gates, n);
+  auto plan = fsv::fusion_plan(L, gates, n, true);
   const int P = (int)plan.size();
   const int cap = *n_passes;
   *n_passes = P;
@@ -1308,7 +1350,7 @@ int sv_host_store_view(int L, const sv_floquet_params* p, int n, int pass, int* 
   if (!fsv::params_valid(L, *p, nullptr)) return SV_EINVAL;
   if (!fsv::block_tc_supported(L, n)) return SV_EINVAL;
   auto gates = fsv::period_gates(L, *p, p->theta, p->hx);
-  auto plan = fsv::fusion_plan(L, gates, n);
+  auto plan = fsv::fusion_plan(L, gates, n, true);
   const int P = (int)plan.size();
   if (pass < 0 || pass >= P) return SV_EINVAL;
   fsv::PassArgs pa;

@@ -182,6 +182,7 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
 // Build the period evolution of chain c in its context for a graph form.
 int build_graph_form(sv_batch* b, int c, int form, int min_tiles) {
   fsv::ctx_set_min_tiles(b->ctx[c], min_tiles);
+  fsv::ctx_set_cyclic(b->ctx[c], false);
   sv_floquet_params p = b->params[c];
   p.theta_p = nullptr;
   p.hx_p = nullptr;

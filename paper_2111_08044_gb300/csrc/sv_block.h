@@ -41,6 +41,7 @@ struct PassArgs {
   // c = 0); nb[j][k]: the other neighbours' sites (-1: none)
   float diag_lin0[8] = {};
   int8_t diag_nb[8][2] = {};
+  int diag_lo = 0;           // window position of the output's layout (0: natural)
   int8_t sigma[16] = {};     // output tile bit of input tile bit q
   // tensor-core pass: TMEM lane m holds tile row XOR over set bits i of m
   // of rowvec[i] (an invertible map, chosen against staging bank conflicts)
@@ -65,6 +66,11 @@ struct PassArgs {
 
 struct BlockPlan {
   int L = 0, n = 0, R = 0, split = 0;
+  int start = 0;  // window of the period's first pass; the layout between periods
+  // launch sequences (indices into args): a period, the last period of an
+  // evolution (its last pass writes the natural layout), and the relabel
+  // steps from the natural layout to the start that begin an evolution
+  std::vector<int> seq_cyc, seq_exit, seq_entry;
   bool tensor_cores = false;
   std::vector<BlockPass> passes;
   std::vector<PassArgs> args;
@@ -89,18 +95,23 @@ struct BlockPlan {
 std::string block_tile_layout(int L, int n, int R, int lo, int lo_next, int* a_out,
                               int8_t* sigma);
 int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, int n,
-                int split, const LaunchCfg& cfg, BlockPlan** out, std::string* msg);
+                int split, const LaunchCfg& cfg, bool cyclic, BlockPlan** out,
+                std::string* msg);
 void block_info(const BlockPlan* bp, int* passes, int* launches);
 // Fold the periodic renormalisation into the period's first pass.
 void block_set_renorm(BlockPlan* bp, const Renorm& rn);
 size_t block_upload_bytes(const BlockPlan* bp);
+// The relabel steps that begin an evolution (none when the start is 0).
+cudaError_t block_enqueue_entry(BlockPlan* bp, void* psi, cudaStream_t s);
+// One period; `last`: the evolution's last period, which hands back the
+// natural layout.
 cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,
-                                 int ring_len, cudaStream_t s);
-// As block_enqueue_period with ev[k] recorded before launch k and
+                                 int ring_len, cudaStream_t s, bool last);
+// As block_enqueue_period with ev[k] recorded before pass k and
 // ev[passes + 1] after the final reduce.
 cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* counter,
                                         double* ring, int ring_len, cudaStream_t s,
-                                        cudaEvent_t* ev);
+                                        cudaEvent_t* ev, bool last);
 void block_free(BlockPlan* bp);
 
 // Nonzero if a tensor-core pass reported a timed-out wait (synchronises s).

@@ -107,6 +107,17 @@ struct Diag {
   }
 };
 
+// Natural index (site i at bit i) of index x in the block layout whose
+// window of n sites starts at site lo: window sites at bits 0..n-1, sites
+// below lo at bits n..n+lo-1, the others in place (lo = 0: natural).
+__device__ __forceinline__ uint64_t to_natural(uint64_t x, int n, int lo) {
+  if (lo == 0) return x;
+  const uint64_t win = x & ((1ull << n) - 1);
+  const uint64_t below = (x >> n) & ((1ull << lo) - 1);
+  const uint64_t rest = x & ~((1ull << (n + lo)) - 1);
+  return (win << lo) | below | rest;
+}
+
 // Deterministic block sum of (e, n) written to out[2*blockIdx.x + {0,1}].
 __device__ inline void block_store_pair(double e, double n, double* out) {
   __shared__ double se[32], sn[32];

@@ -34,6 +34,9 @@ int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out);
 void ctx_advance(sv_ctx* ctx, int64_t periods);
 // Block passes of later builds keep at least `tiles` tiles per CTA.
 void ctx_set_min_tiles(sv_ctx* ctx, int tiles);
+// Whether later block builds may start their periods off site 0 (the batch
+// replays captured periods back to back and needs the natural layout).
+void ctx_set_cyclic(sv_ctx* ctx, bool cyclic);
 // (energy density, norm) of periods c0 .. c0+count-1 from the energy ring.
 int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n);
 // Periods the energy ring holds.
@@ -106,6 +109,9 @@ struct BlockPass {
   std::vector<int> x_sites;   // sites whose <X> this pass measures
   bool diag = false;          // this pass measures the diagonal terms and norm
 };
-std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2> &gates, int n);
+// cyclic: the period may start (and end) at the window s <= 7 that needs the
+// fewest passes instead of at site 0 (passes[0].lo is the start).
+std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2> &gates, int n,
+                                   bool cyclic = false);
 
 }  // namespace fsv

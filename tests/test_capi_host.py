@@ -128,7 +128,9 @@ def test_fused_passes_multiply_to_the_period(svlib, L, n):
     kw = dict(J=1.0, hx=0.9, hz=0.4, T=0.5, K=4, theta=0.3)
     lo, gc, U = _plan(svlib, L, n, **kw)
     assert gc.sum() == 4 * (L - 1)
-    assert lo[0] == 0
+    # a period may start at any window s <= 7: the state stays in that
+    # window's layout between periods; the passes still compose to U_F
+    assert 0 <= lo[0] <= 7
     total = np.eye(1 << L, dtype=np.complex128)
     for k in range(len(lo)):
         total = _window_op(L, lo[k], n, U[k]) @ total
@@ -211,8 +213,8 @@ def test_pass_operands_are_close_to_unitary(svlib, L):
 def test_fusion_plan_shape_large_chains(svlib, L, n):
     lo, gc, _ = _plan(svlib, L, n)
     assert gc.sum() == 4 * (L - 1)
-    assert lo[0] == 0
-    jumps = np.abs(np.diff(np.concatenate([lo, [0]])))
+    assert 0 <= lo[0] <= 7  # one relabel pass reaches the start from site 0
+    jumps = np.abs(np.diff(np.concatenate([lo, lo[:1]])))
     assert jumps.max() <= 7  # every relabel fits in a 7-bit row index
     assert len(lo) <= {6: 21, 7: 18}[n]
 
@@ -265,7 +267,7 @@ def _site_position(L, n, lo, s):
     return n + s if s < lo else s
 
 
-@pytest.mark.parametrize("L", [13, 20, 26, 30, 34])
+@pytest.mark.parametrize("L", [13, 16, 20, 23, 26, 30, 34])
 def test_block_tile_layout_and_row_map(svlib, L):
     """Each pass's relabel sigma follows the window layout rule; the
     tensor-core row map is invertible, keeps the converter's swizzled row
@@ -322,12 +324,14 @@ def test_block_tile_layout_and_row_map(svlib, L):
         assert got <= wavefronts(list(range(128)), list(range(13)))
         assert natural or got < 16
     if L == 30:
-        # relabels that scattered rows across the banks (natural order: 16,
-        # 16, 4, 4 wavefronts) are spread by the row map
-        assert wf[4] == 4 and wf[5] == 2 and wf[11] == 2 and wf[12] == 2
-        # pass 15 sends six row bits above the bank bits: no row map helps
+        # the row map spreads every relabelled write of the L = 30 period
+        # (16 passes from the start at site 2) to at most 4 wavefronts
+        assert max(wf) <= 4
+    if L in (16, 23):
+        # one pass sends six row bits above the bank bits: no row map helps
         # (16 wavefronts), a reordered staging tile does
-        assert list(st[15]) != list(range(13)) and wf[15] == 2
+        k = {16: 6, 23: 11}[L]
+        assert list(st[k]) != list(range(13)) and wf[k] <= 4
 
 
 @pytest.mark.parametrize("L,first", [(6, 0), (7, 1)])
@@ -369,7 +373,8 @@ def _store_view(svlib, L, p, k):
     return r, list(dims)[:r], [8] + list(strides)[:r - 1], list(box)[:r], list(coord)
 
 
-@pytest.mark.parametrize("L,first", [(13, 0), (14, 0), (19, 0), (21, 0), (21, 1), (27, 0), (30, 0)])
+@pytest.mark.parametrize("L,first", [(13, 0), (14, 0), (16, 0), (19, 0), (21, 0), (21, 1), (23, 0),
+                                     (27, 0), (30, 0)])
 def test_tensor_core_store_view_places_every_amplitude(svlib, L, first):
     """The TMA store view of every tensor-core pass, walked on the host: the
     staging element that holds output amplitude y of tile t (staging bit
@@ -426,5 +431,5 @@ def test_tensor_core_store_view_places_every_amplitude(svlib, L, first):
             addr = sum((c[d] + idx[d]) * strides[d] for d in range(rank))
             want = 8 * (x_in | (tlo << n) | (thi << (ak + 7)))
             np.testing.assert_array_equal(addr, want, err_msg=f"pass {k} tile {t}")
-    if (L, first) in ((21, 0), (30, 0)):
+    if (L, first) in ((16, 0), (23, 0)):
         assert restaged > 0

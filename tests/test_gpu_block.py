@@ -85,13 +85,16 @@ def test_tensor_core_100_periods_with_renormalisation(svlib, L):
     assert _infidelity(psi, psi_o) < 1e-5
 
 
-@pytest.mark.parametrize("L,first,ew,periods", [(15, 1, 1.0, 3), (21, 0, 1.0, 2), (26, 1, 0.5, 1)])
+@pytest.mark.parametrize("L,first,ew,periods", [(15, 1, 1.0, 3), (21, 0, 1.0, 2), (23, 0, 0.5, 2),
+                                                (26, 1, 0.5, 1)])
 def test_tensor_core_variants_match_oracle(svlib, L, first, ew, periods):
-    """Odd L, the other layer order and whole edge fields; at L = 21 the last
-    two passes write through a reordered staging tile (a 4-D store view);
-    at L = 26 the CTAs run 54 tiles each (a ragged tail over 152
-    SMs), so the pass instances specialised on what they measure are checked
-    element by element."""
+    """Odd L, the other layer order and whole edge fields; at L = 23 (and
+    L = 16 above) one pass writes through a reordered staging tile (a 4-D or
+    5-D store view); at L = 26 the CTAs run 54 tiles each (a ragged tail over
+    152 SMs), so the pass instances specialised on what they measure are
+    checked element by element.  Most of these plans start their periods off
+    site 0, so every evolution here also runs the relabel into the period
+    layout and the last period's hand-back to the natural layout."""
     cfg = inputs.ChainConfig(L=L, periods=periods, seed=90 + L, first_layer=first,
                              edge_field_weight=ew)
     psi_o, _, e_o, n_o = orc.run_chain(cfg)

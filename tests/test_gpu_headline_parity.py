@@ -4,13 +4,15 @@ One period of the L = 30 chain (Sec. III.A: K Trotter steps of the two
 brickwork layers, then the kick) in the plain and tensor-core block forms,
 every one of the 2^30 amplitudes compared with the FP64 oracle run on the
 host in the same test, plus the period's energy density.  At L = 30 the
-tensor-core form's seventeen passes include pass 15, whose relabelled write
-goes through a reordered staging tile (a 5-D store view), so a wrong store
-of any subset of amplitudes fails here, not only through an energy.
+tensor-core form's period is 16 passes starting at the window of site 2:
+the evolution runs the relabel pass into that layout, the period, and the
+last pass's variant that hands back the natural layout, so a wrong store
+of any subset of amplitudes in any of them fails here, not only through an
+energy.
 
 The oracle's state is 16 GiB (FP64); on a host with less than 96 GiB of
-memory the test runs at L = 28 instead (still 2^15 tiles, 216 tiles per CTA,
-and a reordered staging tile in its plan)."""
+memory the test runs at L = 28 instead (still 2^15 tiles, 216 tiles per
+CTA)."""
 import os
 
 import numpy as np

@@ -227,8 +227,12 @@ int sv_renormalize(sv_ctx *ctx, double *norm2_before);
  * return the state buffer holds psi back at its starting point up to
  * rounding.  grad_theta / grad_hx: host, length P (nullable).
  * energy_density (nullable): f.  Needs 2x the state memory for lambda,
- * allocated by the library.  Errors: SV_EINVAL, SV_ESTATE, SV_ENOMEM,
- * SV_ECUDA, SV_EUNSUPPORTED.
+ * allocated by the library.  The number of periods is not an argument:
+ * the gradient is taken with respect to every per-period parameter, so P is
+ * the length of the theta_p / hx_p arrays given to sv_build_floquet
+ * (n_period_params); to differentiate fewer periods, build with shorter
+ * arrays.  Errors: SV_EINVAL, SV_ESTATE, SV_ENOMEM, SV_ECUDA,
+ * SV_EUNSUPPORTED.
  */
 int sv_adjoint(sv_ctx *ctx, double *grad_theta, double *grad_hx,
                double *energy_density);
@@ -241,7 +245,36 @@ int sv_get_state(sv_ctx *ctx, void *host_dst, size_t bytes);
  * resume); sets the period counter.  Errors as sv_get_state. */
 int sv_set_state(sv_ctx *ctx, const void *host_src, size_t bytes, int64_t period);
 
-/* Periods applied since sv_init / sv_set_state. */
+/*
+ * Checkpoints of long evolutions (the paper runs more than 1e5 periods,
+ * Sec. IV): the state and the period counter in one file.  Layout,
+ * little-endian: bytes 0-7 "FLQSVCK1"; int32 L; int32 precision; int64
+ * period counter; uint64 payload bytes; uint64 checksum of the payload;
+ * uint64 checksum of bytes 0-39; then the 2^L amplitudes in the natural
+ * layout (interleaved re, im, complex64 or complex128).  Checksums:
+ * FNV-1a (64-bit basis and prime) over little-endian 64-bit words.
+ *
+ * sv_save writes the attached state (stream-ordered after earlier calls)
+ * and the counter to `path`, through a 64 MiB pinned host buffer the call
+ * allocates and frees.  Errors: SV_EINVAL (null path, file not writable),
+ * SV_ESTATE (no state), SV_ENOMEM, SV_ECUDA.
+ *
+ * sv_load reads a checkpoint into the attached state buffer (which must
+ * hold it) and sets L and the period counter as sv_init / sv_set_state
+ * would; a built evolution stays valid when its L matches.  The precision
+ * must be the context's.  On a truncated file or a checksum mismatch it
+ * returns SV_EINVAL with the amplitudes overwritten but L and the counter
+ * unchanged.  Errors: SV_EINVAL, SV_ESTATE, SV_ENOMEM, SV_ECUDA.
+ *
+ * sv_checkpoint_info checks a file (header, payload checksum and size)
+ * without a GPU and reports its L, precision and period (each nullable).
+ * Errors: SV_EINVAL.
+ */
+int sv_save(sv_ctx *ctx, const char *path);
+int sv_load(sv_ctx *ctx, const char *path);
+int sv_checkpoint_info(const char *path, int *L, int *precision, int64_t *period);
+
+/* Periods applied since sv_init / sv_set_state / sv_load. */
 int64_t sv_period_counter(const sv_ctx *ctx);
 
 /*

@@ -54,6 +54,8 @@ def _infidelity(ref, psi):
 
 
 def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
+    """Rows of the study, one per `every` periods (a generator: each row is
+    available as soon as its periods have run)."""
     cfg = inputs.ChainConfig(L=L, seed=seed)
     ref = FloquetSimulator(L, precision="c128")
     ref.init_product_state(cfg.spinors())
@@ -64,7 +66,6 @@ def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
         s.init_product_state(cfg.spinors())
         s.build(**chain_params(cfg, **FORMS[name]))
         sims[name] = s
-    rows = []
     done = 0
     while done < periods:
         k = min(every, periods - done)
@@ -76,10 +77,9 @@ def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
             row[name] = {"max_abs_energy_err": float(np.max(np.abs(e - e_ref))),
                          "infidelity": _infidelity(ref, s),
                          "norm_dev": float(n[-1] - 1.0)}
-        rows.append(row)
+        yield row
     for s in list(sims.values()) + [ref]:
         s.close()
-    return rows
 
 
 def echo(L=26, periods=(10, 100, 1000), seed=1, form="block_tc", precision="c64",

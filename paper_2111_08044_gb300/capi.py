@@ -87,6 +87,9 @@ SIGNATURES = {
     "sv_adjoint": ([_vp, _dp, _dp, _dp], _i32),
     "sv_get_state": ([_vp, _vp, _sz], _i32),
     "sv_set_state": ([_vp, _vp, _sz, _i64], _i32),
+    "sv_save": ([_vp, ctypes.c_char_p], _i32),
+    "sv_load": ([_vp, ctypes.c_char_p], _i32),
+    "sv_checkpoint_info": ([ctypes.c_char_p, _ip, _ip, ctypes.POINTER(_i64)], _i32),
     "sv_period_counter": ([_vp], _i64),
     "sv_pass_info": ([_vp, _ip, _ip, _ip], _i32),
     "sv_build_bytes": ([_vp, ctypes.POINTER(_sz)], _i32),

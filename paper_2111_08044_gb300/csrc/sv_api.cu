@@ -1116,6 +1116,10 @@ int sv_get_state(sv_ctx* ctx, void* host_dst, size_t bytes) {
   return SV_OK;
 }
 
+namespace {
+int record_norm(sv_ctx* ctx, int64_t period);
+}  // namespace
+
 int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period) {
   int rc = check_ready(ctx, false);
   if (rc) return rc;
@@ -1130,19 +1134,140 @@ int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period
           "set counter");
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
   ctx->counter = period;
-  if (period > 0 && ctx->built) {
-    // the folded renormalisation of the next period reads the norm recorded
-    // for period - 1: record the norm of the state just set
-    double n2 = 1.0;
-    rc = measure(ctx, nullptr, &n2);
-    if (rc) return rc;
-    const int64_t slot = (period - 1) % kRing;
-    SV_CUDA(cudaMemcpyAsync(ctx->d_ring + 2 * slot + 1, &n2, sizeof(double),
-                            cudaMemcpyHostToDevice, ctx->stream),
-            "record norm");
-    SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  // the folded renormalisation of the next period reads the norm recorded
+  // for period - 1: record the norm of the state just set
+  return record_norm(ctx, period);
+}
+
+namespace {
+// Host staging of checkpoint copies: pinned chunks of 64 MiB.
+struct Pinned {
+  void* p = nullptr;
+  size_t bytes = 0;
+  explicit Pinned(size_t b) {
+    if (cudaMallocHost(&p, b) == cudaSuccess) bytes = b;
+    else {
+      cudaGetLastError();
+      p = nullptr;
+    }
   }
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+constexpr size_t kCkptChunk = (size_t)64 << 20;
+
+// Record the norm of the state just set as that of period - 1, for the
+// folded renormalisation of the next period.
+int record_norm(sv_ctx* ctx, int64_t period) {
+  if (period <= 0 || !ctx->built) return SV_OK;
+  double n2 = 1.0;
+  int rc = measure(ctx, nullptr, &n2);
+  if (rc) return rc;
+  const int64_t slot = (period - 1) % kRing;
+  SV_CUDA(cudaMemcpyAsync(ctx->d_ring + 2 * slot + 1, &n2, sizeof(double),
+                          cudaMemcpyHostToDevice, ctx->stream),
+          "record norm");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
   return SV_OK;
+}
+}  // namespace
+
+int sv_save(sv_ctx* ctx, const char* path) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (!path) return fail(ctx, SV_EINVAL, "null path");
+  DeviceGuard dg(ctx->device);
+  fsv::CkptHeader h;
+  h.L = ctx->L;
+  h.precision = ctx->precision;
+  h.period = ctx->counter;
+  h.payload_bytes = amp_bytes(ctx->precision) << ctx->L;
+  Pinned buf(std::min<size_t>(kCkptChunk, h.payload_bytes));
+  if (!buf.p) return fail(ctx, SV_ENOMEM, "pinned staging buffer");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, SV_EINVAL, "cannot open %s for writing", path);
+  unsigned char hb[fsv::kCkptHeaderBytes] = {};
+  bool ok = std::fwrite(hb, 1, sizeof(hb), f) == sizeof(hb);  // rewritten at the end
+  uint64_t sum = fsv::ckpt_sum_begin();
+  const char* src = static_cast<const char*>(ctx->state);
+  for (uint64_t off = 0; ok && off < h.payload_bytes; off += buf.bytes) {
+    const size_t n = (size_t)std::min<uint64_t>(buf.bytes, h.payload_bytes - off);
+    cudaError_t e = cudaMemcpyAsync(buf.p, src + off, n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return cuda_fail(ctx, e, "copy state");
+    }
+    sum = fsv::ckpt_sum_update(sum, buf.p, n);
+    ok = std::fwrite(buf.p, 1, n, f) == n;
+  }
+  h.payload_sum = sum;
+  fsv::ckpt_encode_header(h, hb);
+  ok = ok && std::fseek(f, 0, SEEK_SET) == 0 && std::fwrite(hb, 1, sizeof(hb), f) == sizeof(hb);
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? SV_OK : fail(ctx, SV_EINVAL, "write to %s failed", path);
+}
+
+int sv_load(sv_ctx* ctx, const char* path) {
+  if (!ctx) return SV_EINVAL;
+  if (!path) return fail(ctx, SV_EINVAL, "null path");
+  if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, SV_EINVAL, "cannot open %s", path);
+  unsigned char hb[fsv::kCkptHeaderBytes];
+  fsv::CkptHeader h;
+  if (std::fread(hb, 1, sizeof(hb), f) != sizeof(hb) || !fsv::ckpt_decode_header(hb, &h)) {
+    std::fclose(f);
+    return fail(ctx, SV_EINVAL, "%s is not a checkpoint (header)", path);
+  }
+  if (h.precision != ctx->precision) {
+    std::fclose(f);
+    return fail(ctx, SV_EINVAL, "checkpoint precision differs from the context's");
+  }
+  if (ctx->state_bytes < h.payload_bytes) {
+    std::fclose(f);
+    return fail(ctx, SV_EINVAL, "state buffer smaller than the checkpoint's %llu bytes",
+                (unsigned long long)h.payload_bytes);
+  }
+  if (ctx->built && ctx->L != h.L) {
+    std::fclose(f);
+    return fail(ctx, SV_EINVAL, "checkpoint L = %d, built evolution L = %d", h.L, ctx->L);
+  }
+  DeviceGuard dg(ctx->device);
+  Pinned buf(std::min<size_t>(kCkptChunk, h.payload_bytes));
+  if (!buf.p) {
+    std::fclose(f);
+    return fail(ctx, SV_ENOMEM, "pinned staging buffer");
+  }
+  uint64_t sum = fsv::ckpt_sum_begin();
+  char* dst = static_cast<char*>(ctx->state);
+  bool ok = true;
+  for (uint64_t off = 0; ok && off < h.payload_bytes; off += buf.bytes) {
+    const size_t n = (size_t)std::min<uint64_t>(buf.bytes, h.payload_bytes - off);
+    ok = std::fread(buf.p, 1, n, f) == n;
+    if (!ok) break;
+    sum = fsv::ckpt_sum_update(sum, buf.p, n);
+    cudaError_t e = cudaMemcpyAsync(dst + off, buf.p, n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      std::fclose(f);
+      return cuda_fail(ctx, e, "copy state");
+    }
+  }
+  ok = ok && std::fgetc(f) == EOF;
+  std::fclose(f);
+  // the amplitudes are in place; the counter and the L only change on success
+  if (!ok || sum != h.payload_sum)
+    return fail(ctx, SV_EINVAL, "%s: payload truncated or checksum mismatch", path);
+  ctx->L = h.L;
+  ctx->inited = true;
+  long long c = h.period;
+  SV_CUDA(cudaMemcpyAsync(ctx->d_counter, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream),
+          "set counter");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  ctx->counter = h.period;
+  return record_norm(ctx, h.period);
 }
 
 int64_t sv_period_counter(const sv_ctx* ctx) { return ctx ? ctx->counter : -1; }

@@ -100,6 +100,22 @@ Observable observable(int L, const sv_floquet_params &p);
 double site_field_share(int L, int i, double ew);
 bool params_valid(int L, const sv_floquet_params &p, std::string *why);
 
+// Checkpoint files (host_checkpoint.cpp): header and payload checksum.
+constexpr size_t kCkptHeaderBytes = 48;
+struct CkptHeader {
+  int L = 0;
+  int precision = 0;
+  int64_t period = 0;
+  uint64_t payload_bytes = 0;
+  uint64_t payload_sum = 0;
+};
+uint64_t ckpt_sum_begin();
+// FNV-1a over little-endian 64-bit words (bytes: a multiple of 8).
+uint64_t ckpt_sum_update(uint64_t h, const void* data, size_t bytes);
+void ckpt_encode_header(const CkptHeader& h, unsigned char out[kCkptHeaderBytes]);
+// Magic, header checksum and field ranges; false if any fails.
+bool ckpt_decode_header(const unsigned char in[kCkptHeaderBytes], CkptHeader* h);
+
 // a3: fusion of one period into n-site block passes (host, FP64).
 struct BlockPass {
   int lo = 0;                 // window = sites lo .. lo+n-1, local bit j = site lo+j

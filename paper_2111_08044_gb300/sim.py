@@ -86,6 +86,14 @@ class FloquetSimulator:
                    "sv_evolve")
         return e[:periods], n[:periods]
 
+    def save(self, path: str):
+        """Checkpoint the state and the period counter (sv_save)."""
+        capi.check(self._lib.sv_save(self._ctx, str(path).encode()), self._ctx, "sv_save")
+
+    def load(self, path: str):
+        """Resume from a checkpoint (sv_load): state, L and period counter."""
+        capi.check(self._lib.sv_load(self._ctx, str(path).encode()), self._ctx, "sv_load")
+
     def energy(self) -> Tuple[float, float]:
         e = ctypes.c_double()
         n = ctypes.c_double()

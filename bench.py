@@ -52,8 +52,8 @@ def _parse():
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batch-periods", type=int, default=64,
-                    help="periods of the 512-chain batch line (0 skips it)")
+    ap.add_argument("--batch-periods", type=int, default=2000,
+                    help="periods of the 512-chain batch line (the config's 2000; 0 skips it)")
     return ap.parse_args()
 
 
@@ -160,6 +160,8 @@ def _time_form(args, mode, steps, rank, world, local):
     kw = chain_params(cfg)
     if mode == "block":
         kw.update(mode=capi.SV_MODE_BLOCK, block_n=args.n, split=split)
+    elif mode == "multigate":
+        kw.update(mode=capi.SV_MODE_MULTIGATE)
     sim = FloquetSimulator(cfg.L, device=local)
     sim.init_product_state(cfg.spinors())
     sim.build(**kw)
@@ -204,6 +206,7 @@ def _time_form(args, mode, steps, rank, world, local):
         "avg_pass_ms": avg_pass_s * 1e3,
         "pass_gbs": bytes_per_pass / avg_pass_s / 1e9,
         "pass_share": float(pass_ms.sum() / ms.sum()),
+        "pass_ms_each": [round(float(x) / steps, 4) for x in pass_ms],
         "energy_last": float(e[-1]),
         "norm_last": float(n[-1]),
     }
@@ -263,12 +266,17 @@ def _batch(args, local):
     torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     forms = b.forms()
+    widths = b.widths()
     Ls = np.array([c.L for c in chains])
     amps = float(sum(1 << int(L) for L in Ls))
     b.close()
     del b
     torch.cuda.empty_cache()
-    names = {0: "plain", 1: "block_simt", 2: "block_tc", 3: "resident"}
+    names = {0: "plain", 1: "block_simt", 2: "block_tc", 3: "resident", 4: "multigate"}
+    by_L = {}
+    for L in sorted(set(Ls.tolist())):
+        c = int(np.nonzero(Ls == L)[0][0])
+        by_L[str(L)] = names[int(forms[c])] + (f" n={int(widths[c])}" if widths[c] else "")
     return {
         "workload": "512 chains, L uniform 14..22, J~U[0.8,1.2] hx~U[0.6,1.0] hz~U[0.2,0.6] "
                     "theta~U[0.1,0.5], random product states (seed 2), complex64",
@@ -277,7 +285,8 @@ def _batch(args, local):
         "ms": ms,
         "create_and_autotune_s": t_create,
         "amplitudes": amps,
-        "forms": {names[k]: int((forms == k).sum()) for k in range(4) if (forms == k).any()},
+        "forms": {names[k]: int((forms == k).sum()) for k in range(5) if (forms == k).any()},
+        "form_by_L": by_L,
         "norm_max_dev": float(np.abs(n - 1.0).max()),
     }
 
@@ -364,6 +373,17 @@ def _oracle_period_groups(L: int, seed: int):
 TC_TRAFFIC_L28 = 2147.9e6 + 2084.1e6
 
 
+# FP32 pipe of one GB300: 152 SMs x 128 FMA lanes x 2 flops x 2.07 GHz.
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _mg_fp32_tflops(L, form):
+    """Algorithmic FP32 rate of the multi-gate form: each gate costs 32 FMA
+    per amplitude (the FP32 table and its residual), 4(L-1) gates a period."""
+    flops = 2.0 * 32 * (1 << L) * form["gates_per_period"]
+    return flops * form["periods_per_s"] / 1e12
+
+
 def _traffic(args):
     if args.split != "bf16x3" or args.n != 6:
         return None
@@ -447,11 +467,14 @@ def run_ours(args):
     capi.load()
     hbm_peak, bf16_peak, peak_src = _peaks()
     plain_steps = args.plain_steps if args.plain_steps is not None else max(2, args.steps // 3)
+    mg_steps = max(2, args.steps // 4)
     clocks = Clocks(local)
     clocks.start()
     block = _time_form(args, "block", args.steps, rank, world, local)
     plain = _time_form(args, "plain", plain_steps, rank, world, local)
+    multigate = _time_form(args, "multigate", mg_steps, rank, world, local)
     ck = clocks.stop()
+    plain.pop("pass_ms_each", None)  # 116 gate passes: the mean is enough
     t_block = _max_over_ranks(block["elapsed_ms"], world)
     t_plain = _max_over_ranks(plain["elapsed_ms"], world)
     value = world * args.steps / (t_block / 1e3)
@@ -475,7 +498,8 @@ def run_ours(args):
     # plus the relabel launch that begins an evolution whose periods start
     # off site 0 (one per timed call)
     gpl = (block["launches_per_period"] * args.steps + block["entry_launches"]
-           + plain["launches_per_period"] * plain_steps)
+           + plain["launches_per_period"] * plain_steps
+           + multigate["launches_per_period"] * mg_steps)
     achieved = block["pass_gbs"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -490,9 +514,14 @@ def run_ours(args):
                      "peak_source": peak_src},
         "block": {k: block[k] for k in ("periods_per_s", "passes_per_period",
                                         "gates_per_period", "avg_pass_ms", "pass_gbs",
-                                        "pass_share", "energy_last")},
+                                        "pass_share", "energy_last", "pass_ms_each")},
         "plain": dict(plain, periods_per_s=plain_value, steps=plain_steps,
                       roofline_frac=plain["pass_gbs"] / hbm_peak),
+        "multigate": dict(multigate, steps=mg_steps,
+                          periods_per_s=world * mg_steps / (
+                              _max_over_ranks(multigate["elapsed_ms"], world) / 1e3),
+                          fp32_tflops=_mg_fp32_tflops(args.L, multigate),
+                          fp32_frac_of_pipe=_mg_fp32_tflops(args.L, multigate) / FP32_TFLOPS),
         "two_qubit_gates_per_s": value * block["gates_per_period"] / world * world,
         "gpu_launches": gpl,
         "clocks": ck,

@@ -60,6 +60,7 @@ extern "C" {
 /* evolution form */
 #define SV_MODE_PLAIN 0 /* one kernel pass per two-qubit gate */
 #define SV_MODE_BLOCK 1 /* fused n-qubit blocks on the tensor cores */
+#define SV_MODE_MULTIGATE 2 /* many gates per pass on a shared-memory tile (CUDA cores) */
 
 /* arithmetic of the block form */
 #define SV_SPLIT_BF16X3 0 /* tensor cores: 3 exact bf16 digits per operand, exact level-0 sum */
@@ -77,7 +78,7 @@ typedef struct sv_floquet_params {
   double edge_field_weight; /* field share of an open end site (0.5: uniform) */
   int32_t K;                /* Trotter steps per period, >= 1 */
   int32_t first_layer;      /* 0: bonds (0,1),(2,3),.. first; 1: odd bonds first */
-  int32_t mode;             /* SV_MODE_PLAIN or SV_MODE_BLOCK */
+  int32_t mode;             /* SV_MODE_PLAIN, SV_MODE_BLOCK or SV_MODE_MULTIGATE */
   int32_t block_n;          /* block width n for SV_MODE_BLOCK (2..7); 0 = default */
   int32_t split;            /* SV_SPLIT_* (block mode) */
   int32_t renorm_every;     /* rescale psi to unit norm at the start of every this
@@ -433,18 +434,22 @@ int sv_host_store_view(int L, const sv_floquet_params *p, int n, int pass, int *
  * Many independent chains (each its own L, parameters and product state)
  * evolved together on one device.  Chains of up to 14 sites can stay in one
  * CTA's shared memory for a whole run (resident form); the others run the
- * plain or block forms.  One CUDA graph advances every chain by a run of
- * periods, the chains as independent branches.  An autotuner times the
- * forms that fit each distinct L on a few of its chains and keeps the
- * fastest (chain-periods per second).
+ * plain, block or multi-gate forms.  One CUDA graph advances every chain by
+ * a run of periods, the chains as independent branches (within a run a
+ * chain's block periods may start off site 0; every run hands back the
+ * natural layout).  An autotuner times the forms that fit each distinct L,
+ * with their block widths and tile runs, on a few of its chains and keeps
+ * the fastest (chain-periods per second).
  */
 typedef struct sv_batch sv_batch;
 
 #define SV_BATCH_AUTO (-1)      /* autotune per distinct L */
 #define SV_BATCH_PLAIN 0        /* per-gate passes */
-#define SV_BATCH_BLOCK_SIMT 1   /* fused n = 6 windows on CUDA cores */
+#define SV_BATCH_BLOCK_SIMT 1   /* fused windows on CUDA cores: n = 5..7 chosen by the
+                                   autotuner, n = 6 when the form is forced */
 #define SV_BATCH_BLOCK_TC 2     /* fused n = 6 windows on the tensor cores (L >= 13) */
 #define SV_BATCH_RESIDENT 3     /* state in one CTA's shared memory (L <= 14) */
+#define SV_BATCH_MULTIGATE 4    /* many gates per pass on a shared-memory tile */
 
 /* Bytes of the state buffer for n_chains chains of sizes L[0..n_chains):
  * complex64 states back to back, each starting on a 256-byte boundary. */
@@ -471,6 +476,10 @@ int sv_batch_evolve(sv_batch *b, int64_t periods, double *energy_out, double *no
 
 /* The SV_BATCH_* form each chain runs (host array of n_chains). */
 int sv_batch_forms(const sv_batch *b, int *form_out);
+
+/* The block width n of each chain's form (host array of n_chains; 0 for
+ * the plain, resident and multi-gate forms). */
+int sv_batch_widths(const sv_batch *b, int *n_out);
 
 const char *sv_batch_last_error(const sv_batch *b);
 void sv_batch_destroy(sv_batch *b);

@@ -25,6 +25,7 @@ SV_C64 = 0
 SV_C128 = 1
 SV_MODE_PLAIN = 0
 SV_MODE_BLOCK = 1
+SV_MODE_MULTIGATE = 2
 SV_SPLIT_BF16X3 = 0
 SV_SPLIT_FP32 = 1
 SV_BATCH_AUTO = -1
@@ -32,6 +33,7 @@ SV_BATCH_PLAIN = 0
 SV_BATCH_BLOCK_SIMT = 1
 SV_BATCH_BLOCK_TC = 2
 SV_BATCH_RESIDENT = 3
+SV_BATCH_MULTIGATE = 4
 
 _ERRNAMES = {SV_EINVAL: "SV_EINVAL", SV_ENOMEM: "SV_ENOMEM", SV_ECUDA: "SV_ECUDA",
              SV_ETIMEOUT: "SV_ETIMEOUT", SV_ESTATE: "SV_ESTATE",
@@ -112,6 +114,7 @@ SIGNATURES = {
                         _i32),
     "sv_batch_evolve": ([_vp, _i64, _dp, _dp], _i32),
     "sv_batch_forms": ([_vp, _ip], _i32),
+    "sv_batch_widths": ([_vp, _ip], _i32),
     "sv_batch_last_error": ([_vp], ctypes.c_char_p),
     "sv_batch_destroy": ([_vp], None),
 }

@@ -210,7 +210,8 @@ bool params_valid(int L, const sv_floquet_params &p, std::string *why) {
       !std::isfinite(p.T) || !std::isfinite(p.theta) ||
       !std::isfinite(p.edge_field_weight))
     return bad("non-finite parameter");
-  if (p.mode != SV_MODE_PLAIN && p.mode != SV_MODE_BLOCK) return bad("unknown mode");
+  if (p.mode != SV_MODE_PLAIN && p.mode != SV_MODE_BLOCK && p.mode != SV_MODE_MULTIGATE)
+    return bad("unknown mode");
   if (p.renorm_every < 0) return bad("renorm_every must be >= 0");
   if (p.n_period_params < 0) return bad("n_period_params must be >= 0");
   if (p.n_period_params > 0 && !p.theta_p && !p.hx_p)

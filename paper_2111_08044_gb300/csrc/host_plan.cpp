@@ -237,6 +237,47 @@ Hist cached_plan(const Dag& dag, int L, int n, int ng, bool cyclic) {
 
 }  // namespace
 
+std::vector<MultiPass> multigate_plan(int L, const std::vector<Gate2>& gates, int w) {
+  // Greedy: each pass takes the window of w sites that absorbs the most
+  // pending gates (the lowest such window on ties).  The state keeps the
+  // natural layout, so a window may move anywhere between passes.
+  const Dag dag = make_dag(gates, L);
+  const int ng = (int)gates.size();
+  std::vector<uint64_t> done((ng + 63) / 64, 0);
+  int count = 0;
+  std::vector<MultiPass> out;
+  std::vector<int> last_gate(L, -1);
+  for (int k = 0; k < ng; ++k) {
+    last_gate[gates[k].bond] = k;
+    last_gate[gates[k].bond + 1] = k;
+  }
+  while (count < ng) {
+    int best_lo = -1;
+    std::vector<int> best;
+    for (int lo = 0; lo + w <= L; ++lo) {
+      std::vector<uint64_t> d = done;
+      std::vector<int> ab = absorb(dag, d, lo, w);
+      if (ab.size() > best.size()) {
+        best.swap(ab);
+        best_lo = lo;
+      }
+    }
+    if (best.empty()) break;  // cannot happen for a gate DAG of bonds inside the chain
+    for (int g : best) set(done, g);
+    count += (int)best.size();
+    MultiPass p;
+    p.lo = best_lo;
+    p.gates = best;
+    for (int g : best)
+      for (int site : {gates[g].bond, gates[g].bond + 1})
+        if (last_gate[site] == g) p.x_sites.push_back(site);
+    std::sort(p.x_sites.begin(), p.x_sites.end());
+    out.push_back(std::move(p));
+  }
+  if (!out.empty()) out.back().diag = true;
+  return out;
+}
+
 std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2>& gates, int n, bool cyclic) {
   const Dag dag = make_dag(gates, L);
   const int ng = (int)gates.size();

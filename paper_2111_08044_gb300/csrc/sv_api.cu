@@ -59,6 +59,8 @@ struct sv_ctx {
   double* d_meas = nullptr;
   long long* d_counter = nullptr;
   fsv::BlockPlan* block = nullptr;  // block-mode plan and buffers
+  std::vector<fsv::MultiArgs> mg;   // multi-gate passes of a period
+  int* d_mg = nullptr;              // their gate indices and tile bits
 
   cudaGraphExec_t graph = nullptr;       // one period
   cudaGraphExec_t graph_exit = nullptr;  // an evolution's last period (block plans
@@ -133,6 +135,9 @@ void free_build(sv_ctx* ctx) {
   ctx->d_gates_bytes = 0;
   cudaFree(ctx->d_part_evolve);
   ctx->d_part_evolve = nullptr;
+  cudaFree(ctx->d_mg);
+  ctx->d_mg = nullptr;
+  ctx->mg.clear();
   if (ctx->block) {
     fsv::block_free(ctx->block);
     ctx->block = nullptr;
@@ -167,8 +172,28 @@ fsv::Renorm renorm_of(const sv_ctx* ctx) {
   return rn;
 }
 
+// Enqueue one multi-gate period on stream s; ev (nullable) as for the
+// profiled plain period, one event before each pass.
+int enqueue_multigate_period(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev) {
+  const size_t P = ctx->mg.size();
+  for (size_t k = 0; k < P; ++k) {
+    fsv::MultiArgs ma = ctx->mg[k];
+    if (k == 0) ma.ep.rn = renorm_of(ctx);
+    if (ev) SV_CUDA(cudaEventRecord(ev[k], s), "event record");
+    SV_CUDA(fsv::launch_multigate(ma, ctx->state, ctx->cfg, s), "multi-gate launch");
+  }
+  if (ev) SV_CUDA(cudaEventRecord(ev[P], s), "event record");
+  SV_CUDA(fsv::launch_period_reduce(ctx->d_part_evolve,
+                                    (long long)ctx->part_slots_evolve * ctx->maxb, ctx->L,
+                                    ctx->d_ring, kRing, ctx->d_counter, 1, s),
+          "period reduce launch");
+  if (ev) SV_CUDA(cudaEventRecord(ev[P + 1], s), "event record");
+  return SV_OK;
+}
+
 // Enqueue one plain-mode period on stream s.
 int enqueue_plain_period(sv_ctx* ctx, cudaStream_t s) {
+  if (ctx->params.mode == SV_MODE_MULTIGATE) return enqueue_multigate_period(ctx, s, nullptr);
   const int ng = (int)ctx->gates.size();
   const size_t cbytes = amp_bytes(ctx->precision);
   const long long stride = ctx->n_period_params > 0 ? (long long)ng * fsv::kGateEntries : 0;
@@ -253,13 +278,19 @@ int read_ring(sv_ctx* ctx, int64_t c0, int64_t count, double* e_out, double* n_o
 // Hooks for the batch executor (sv_batch.cu); not part of the C ABI.
 namespace fsv {
 
-int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out) {
+int ctx_capture_run(sv_ctx* ctx, int64_t periods, cudaGraph_t* out) {
   *out = nullptr;
   if (!ctx || !ctx->built) return SV_ESTATE;
   DeviceGuard dg(ctx->device);
   SV_CUDA(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed),
           "begin capture");
-  int rc = enqueue_period(ctx, ctx->cap_stream);
+  int rc = SV_OK;
+  if (off_natural(ctx) && periods > 0) {
+    cudaError_t e = fsv::block_enqueue_entry(ctx->block, ctx->state, ctx->cap_stream);
+    if (e != cudaSuccess) rc = cuda_fail(ctx, e, "relabel launch");
+  }
+  for (int64_t k = 0; k < periods && rc == SV_OK; ++k)
+    rc = enqueue_period(ctx, ctx->cap_stream, k + 1 == periods);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
   if (rc != SV_OK) {
@@ -554,6 +585,7 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev, bool l
     if (e != cudaSuccess) return cuda_fail(ctx, e, "block period launch");
     return SV_OK;
   }
+  if (ctx->params.mode == SV_MODE_MULTIGATE) return enqueue_multigate_period(ctx, s, ev);
   const int ng = (int)ctx->gates.size();
   const size_t cbytes = amp_bytes(ctx->precision);
   const long long stride = ctx->n_period_params > 0 ? (long long)ng * fsv::kGateEntries : 0;
@@ -586,6 +618,68 @@ int enqueue_period_profiled(sv_ctx* ctx, cudaStream_t s, cudaEvent_t* ev, bool l
 // over one-ulp moves of each entry that lowers the distance of the FP32
 // matrix from unitarity (a plain rounding leaves a defect whose sign repeats
 // every time the gate is applied, so the norm would drift steadily).
+
+// The multi-gate passes of a period: per pass its gates' indices and tile
+// bits (one device array for all passes), the sites whose <X> it measures,
+// and the diagonal part on the period's last pass.
+int build_multigate(sv_ctx* ctx, const std::vector<fsv::MultiPass>& plan) {
+  const int L = ctx->L;
+  const int tb = L < fsv::kMgTileBits ? L : fsv::kMgTileBits;
+  std::vector<int> idx;
+  std::vector<size_t> at;
+  for (const auto& mp : plan) {
+    at.push_back(idx.size());
+    for (int g : mp.gates) idx.push_back(g);
+    const int A = L <= fsv::kMgTileBits ? 4 : std::max(mp.lo, 4);
+    for (int g : mp.gates) {
+      const int b = ctx->gates[g].bond;
+      idx.push_back(b < 4 ? b : b - A + 4);
+    }
+  }
+  if (!idx.empty()) {
+    if (cudaMalloc(&ctx->d_mg, sizeof(int) * idx.size()) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->d_mg = nullptr;
+      return fail(ctx, SV_ENOMEM, "multi-gate plan allocation failed");
+    }
+    SV_CUDA(cudaMemcpy(ctx->d_mg, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice),
+            "upload multi-gate plan");
+  }
+  SV_CUDA(fsv::multigate_prepare(), "multi-gate shared-memory opt-in");
+  const int ng = (int)ctx->gates.size();
+  int slot = 0;
+  for (size_t k = 0; k < plan.size(); ++k) {
+    const fsv::MultiPass& mp = plan[k];
+    fsv::MultiArgs ma;
+    ma.L = L;
+    ma.tb = tb;
+    ma.A = L <= fsv::kMgTileBits ? 4 : std::max(mp.lo, 4);
+    ma.ngates = (int)mp.gates.size();
+    ma.gidx = ctx->d_mg + at[k];
+    ma.gq = ctx->d_mg + at[k] + mp.gates.size();
+    ma.gates = static_cast<const float2*>(ctx->d_gates);
+    ma.stride = ctx->n_period_params > 0 ? (long long)ng * fsv::kGateEntries : 0;
+    ma.counter = ctx->d_counter;
+    const bool measures = !ctx->obs.general && (!mp.x_sites.empty() || mp.diag);
+    if (measures) {
+      for (int site : mp.x_sites) {
+        if (ma.nx >= fsv::kMgMaxX) return fail(ctx, SV_EINVAL, "too many measured sites");
+        ma.xq[ma.nx] = site < 4 ? site : site - ma.A + 4;
+        ma.xc[ma.nx] = (float)ctx->obs.cx[site];
+        ++ma.nx;
+      }
+      ma.diag = mp.diag ? 1 : 0;
+      ma.ep = epi_for(ctx, mp.diag ? fsv::EPI_DIAG : 0, 0,
+                      ctx->d_part_evolve + (size_t)slot * ctx->maxb * 2);
+      ++slot;
+    }
+    ctx->mg.push_back(ma);
+  }
+  ctx->passes_per_period = (int)plan.size();
+  ctx->launches_per_period = (int)plan.size() + 1;
+  ctx->build_bytes = ctx->d_gates_bytes + sizeof(int) * idx.size();
+  return SV_OK;
+}
 
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<float2>& out, size_t at) {
   for (size_t g = 0; g < gates.size(); ++g) {
@@ -728,6 +822,8 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
     return fail(ctx, SV_EUNSUPPORTED, "per-period parameters need SV_MODE_PLAIN");
   if (p->mode == SV_MODE_BLOCK && ctx->precision != SV_C64)
     return fail(ctx, SV_EUNSUPPORTED, "block mode needs SV_C64");
+  if (p->mode == SV_MODE_MULTIGATE && ctx->precision != SV_C64)
+    return fail(ctx, SV_EUNSUPPORTED, "multi-gate mode needs SV_C64");
   DeviceGuard dg(ctx->device);
   free_build(ctx);
   ctx->params = *p;
@@ -772,7 +868,15 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
       return fail(ctx, SV_ENOMEM, "gate table allocation failed");
     }
     int slots = 0;
-    for (auto& g : ctx->gates) slots += g.epi ? 1 : 0;
+    std::vector<fsv::MultiPass> mplan;
+    if (p->mode == SV_MODE_MULTIGATE) {
+      const int w = ctx->L <= fsv::kMgTileBits ? ctx->L : fsv::kMgWindow;
+      mplan = fsv::multigate_plan(ctx->L, ctx->gates, w);
+      for (auto& mp : mplan)
+        slots += !ctx->obs.general && (!mp.x_sites.empty() || mp.diag) ? 1 : 0;
+    } else {
+      for (auto& g : ctx->gates) slots += g.epi ? 1 : 0;
+    }
     ctx->part_slots_evolve = slots;
     size_t pbytes = sizeof(double) * 2 * (size_t)ctx->maxb * slots;
     if (cudaMalloc(&ctx->d_part_evolve, pbytes) != cudaSuccess) {
@@ -807,6 +911,10 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
     ctx->passes_per_period = ng;
     ctx->launches_per_period = ng + 1;
     ctx->build_bytes = ctx->d_gates_bytes;
+    if (p->mode == SV_MODE_MULTIGATE) {
+      int rc = build_multigate(ctx, mplan);
+      if (rc) return rc;
+    }
   }
   ctx->built = true;
   return SV_OK;

@@ -3,17 +3,21 @@
 // caller-owned buffer.
 //
 // Every chain gets a context (sv_ctx) on its slice for initialisation and,
-// for the plain and block forms, for its period graph.  Chains of at most
+// for the plain, block and multi-gate forms, for its evolution graph.  Chains of at most
 // 14 sites may instead run the resident form (k_batch.cu): one launch
 // advances all of them, each in one CTA's shared memory.  An evolution is
 // one CUDA graph per run of M periods: the resident launch and, for every
-// other chain, M copies of its period graph in sequence, the chains as
-// independent branches.
+// other chain, its run of M periods captured from its context (a block plan
+// whose periods start off site 0 relabels into its period layout at the
+// start of the run and hands back the natural layout at its end), the
+// chains as independent branches.
 //
 // The autotuner (form SV_BATCH_AUTO) times every form that fits a distinct
-// L, run together for four periods through the same kind of graph (block
-// forms with 4, 8 or 16 tiles per CTA at least), and keeps the fastest (most
-// chain-periods per second) for all chains of that L.  The resident form is
+// L, run together for four periods through the same kind of graph (the
+// tensor-core block form with 4, 8 or 16 tiles per CTA at least, the
+// CUDA-core block form at widths n = 5, 6 and 7, the plain, multi-gate and
+// resident forms), and keeps the fastest (most chain-periods per second)
+// for all chains of that L.  The resident form is
 // timed on all chains of that L (one CTA each, so its rate grows with their
 // number); the others, which fill the device with one chain, on up to eight.
 #include <cuda_runtime.h>
@@ -39,6 +43,7 @@ struct sv_batch {
   std::vector<size_t> off;
   std::vector<int> form;
   std::vector<int> min_tiles;  // block forms: tiles per CTA at least
+  std::vector<int> width;      // block forms: window width n
   std::vector<sv_floquet_params> params;
   std::vector<const double*> spinors;  // caller's arrays, valid during create only
   std::vector<sv_ctx*> ctx;
@@ -65,6 +70,8 @@ constexpr size_t kAlign = 256;
 // autotuner picks the run length per L among these.
 constexpr int kTileRuns[3] = {4, 8, 16};
 constexpr int kDefaultTileRun = 8;
+constexpr int kSimtWidths[3] = {5, 6, 7};
+constexpr int kDefaultWidth = 6;
 
 int bfail(sv_batch* b, int code, const char* fmt, ...) {
   if (b) {
@@ -90,6 +97,7 @@ bool form_fits(int form, int L) {
     case SV_BATCH_BLOCK_SIMT: return L >= 6;
     case SV_BATCH_BLOCK_TC: return L >= 13;
     case SV_BATCH_RESIDENT: return L <= fsv::kResidentMaxL;
+    case SV_BATCH_MULTIGATE: return true;
     default: return false;
   }
 }
@@ -179,10 +187,10 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
   return SV_OK;
 }
 
-// Build the period evolution of chain c in its context for a graph form.
-int build_graph_form(sv_batch* b, int c, int form, int min_tiles) {
+// Build the period evolution of chain c in its context for a graph form
+// (block forms: window width n, at least min_tiles tiles per CTA).
+int build_graph_form(sv_batch* b, int c, int form, int min_tiles, int n) {
   fsv::ctx_set_min_tiles(b->ctx[c], min_tiles);
-  fsv::ctx_set_cyclic(b->ctx[c], false);
   sv_floquet_params p = b->params[c];
   p.theta_p = nullptr;
   p.hx_p = nullptr;
@@ -190,9 +198,11 @@ int build_graph_form(sv_batch* b, int c, int form, int min_tiles) {
   p.renorm_every = 0;
   if (form == SV_BATCH_PLAIN) {
     p.mode = SV_MODE_PLAIN;
+  } else if (form == SV_BATCH_MULTIGATE) {
+    p.mode = SV_MODE_MULTIGATE;
   } else {
     p.mode = SV_MODE_BLOCK;
-    p.block_n = 6;
+    p.block_n = form == SV_BATCH_BLOCK_TC ? 6 : n;
     p.split = form == SV_BATCH_BLOCK_TC ? SV_SPLIT_BF16X3 : SV_SPLIT_FP32;
   }
   int rc = sv_build_floquet(b->ctx[c], &p);
@@ -232,19 +242,13 @@ int make_graph(sv_batch* b, const std::vector<int>& chains, const ResidentSet* r
   }
   for (int c : chains) {
     cudaGraph_t pg = nullptr;
-    int rc = fsv::ctx_capture_period(b->ctx[c], &pg);
+    int rc = fsv::ctx_capture_run(b->ctx[c], periods, &pg);
     if (rc) return fail_g(bfail(b, rc, "chain %d capture: %s", c, sv_last_error(b->ctx[c])));
-    cudaGraphNode_t prev = nullptr;
-    for (int k = 0; k < periods; ++k) {
-      cudaGraphNode_t node;
-      cudaError_t e = cudaGraphAddChildGraphNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, pg);
-      if (e != cudaSuccess) {
-        cudaGraphDestroy(pg);
-        return fail_g(bfail(b, SV_ECUDA, "chain node: %s", cudaGetErrorString(e)));
-      }
-      prev = node;
-    }
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, pg);
     cudaGraphDestroy(pg);
+    if (e != cudaSuccess)
+      return fail_g(bfail(b, SV_ECUDA, "chain node: %s", cudaGetErrorString(e)));
   }
   cudaError_t e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
@@ -265,7 +269,7 @@ int reinit(sv_batch* b, int c) {
 // sample[i] in form forms[i] (block forms with at least tiles[i] tiles per
 // CTA).  The trial moves the states; they are initialised again after it.
 int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<int>& forms,
-               const std::vector<int>& tiles, double* rate) {
+               const std::vector<int>& tiles, int n, double* rate) {
   *rate = 0.0;
   constexpr int kPeriods = 4;
   ResidentSet rs;
@@ -275,7 +279,7 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
     if (forms[i] == SV_BATCH_RESIDENT) {
       res_chains.push_back(sample[i]);
     } else {
-      rc = build_graph_form(b, sample[i], forms[i], tiles[i]);
+      rc = build_graph_form(b, sample[i], forms[i], tiles[i], n);
       graph_chains.push_back(sample[i]);
     }
   }
@@ -306,10 +310,10 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
   return rc;
 }
 
-int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles,
+int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles, int n,
               double* rate) {
   return time_forms(b, sample, std::vector<int>(sample.size(), form),
-                    std::vector<int>(sample.size(), min_tiles), rate);
+                    std::vector<int>(sample.size(), min_tiles), n, rate);
 }
 
 int autotune(sv_batch* b) {
@@ -319,29 +323,36 @@ int autotune(sv_batch* b) {
     const int L = kv.first;
     std::vector<int> sample(kv.second.begin(),
                             kv.second.begin() + std::min<size_t>(8, kv.second.size()));
-    int best = SV_BATCH_PLAIN, best_tiles = kDefaultTileRun;
+    int best = SV_BATCH_PLAIN, best_tiles = kDefaultTileRun, best_n = 0;
     double best_rate = -1.0;
-    for (int f : {SV_BATCH_RESIDENT, SV_BATCH_BLOCK_TC, SV_BATCH_BLOCK_SIMT, SV_BATCH_PLAIN}) {
+    for (int f : {SV_BATCH_RESIDENT, SV_BATCH_BLOCK_TC, SV_BATCH_BLOCK_SIMT, SV_BATCH_PLAIN,
+                  SV_BATCH_MULTIGATE}) {
       if (!form_fits(f, L)) continue;
-      const bool block = f == SV_BATCH_BLOCK_TC || f == SV_BATCH_BLOCK_SIMT;
       for (int t : kTileRuns) {
-        if (!block && t != kDefaultTileRun) continue;
-        // a resident chain uses one CTA, so its form scales with the chain
-        // count up to the SM count: it is timed on every chain of this L;
-        // the other forms fill the device with one chain's passes
-        double rate = 0.0;
-        int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, t, &rate);
-        if (rc) return rc;
-        if (rate > best_rate) {
-          best_rate = rate;
-          best = f;
-          best_tiles = t;
+        // tile runs for the tensor-core form, widths for the CUDA-core one
+        if (f != SV_BATCH_BLOCK_TC && t != kDefaultTileRun) continue;
+        for (int n : kSimtWidths) {
+          if (f != SV_BATCH_BLOCK_SIMT && n != kDefaultWidth) continue;
+          if (f == SV_BATCH_BLOCK_SIMT && n > L) continue;
+          // a resident chain uses one CTA, so its form scales with the chain
+          // count up to the SM count: it is timed on every chain of this L;
+          // the other forms fill the device with one chain's passes
+          double rate = 0.0;
+          int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, t, n, &rate);
+          if (rc) return rc;
+          if (rate > best_rate) {
+            best_rate = rate;
+            best = f;
+            best_tiles = t;
+            best_n = f == SV_BATCH_BLOCK_TC ? 6 : (f == SV_BATCH_BLOCK_SIMT ? n : 0);
+          }
         }
       }
     }
     for (int c : kv.second) {
       b->form[c] = best;
       b->min_tiles[c] = best_tiles;
+      b->width[c] = best_n;
     }
   }
   return SV_OK;
@@ -353,7 +364,8 @@ int setup(sv_batch* b) {
     if (b->form[c] == SV_BATCH_RESIDENT) {
       b->res.push_back(c);
     } else {
-      int rc = build_graph_form(b, c, b->form[c], b->min_tiles[c]);
+      int rc = build_graph_form(b, c, b->form[c], b->min_tiles[c],
+                                b->width[c] > 0 ? b->width[c] : kDefaultWidth);
       if (rc) return rc;
     }
   }
@@ -414,7 +426,7 @@ int sv_batch_create(sv_batch** out, int device, int n_chains, const int* L,
   if (!out) return SV_EINVAL;
   *out = nullptr;
   if (n_chains <= 0 || !L || !params || !product_states || !state_dev) return SV_EINVAL;
-  if (form < SV_BATCH_AUTO || form > SV_BATCH_RESIDENT) return SV_EINVAL;
+  if (form < SV_BATCH_AUTO || form > SV_BATCH_MULTIGATE) return SV_EINVAL;
   const size_t need = sv_batch_state_bytes(n_chains, L);
   if (need == 0 || bytes < need) return SV_EINVAL;
   if (reinterpret_cast<uintptr_t>(state_dev) % kAlign != 0) return SV_EINVAL;
@@ -456,10 +468,15 @@ int sv_batch_create(sv_batch** out, int device, int n_chains, const int* L,
   if (rc == SV_OK) {
     b->form.assign(n_chains, SV_BATCH_PLAIN);
     b->min_tiles.assign(n_chains, kDefaultTileRun);
+    b->width.assign(n_chains, 0);
     if (form == SV_BATCH_AUTO) {
       rc = autotune(b);
     } else {
-      for (int c = 0; c < n_chains; ++c) b->form[c] = form_fits(form, L[c]) ? form : SV_BATCH_PLAIN;
+      for (int c = 0; c < n_chains; ++c) {
+        b->form[c] = form_fits(form, L[c]) ? form : SV_BATCH_PLAIN;
+        if (b->form[c] == SV_BATCH_BLOCK_TC || b->form[c] == SV_BATCH_BLOCK_SIMT)
+          b->width[c] = kDefaultWidth;
+      }
     }
   }
   if (rc == SV_OK) rc = setup(b);
@@ -541,6 +558,12 @@ int sv_batch_evolve(sv_batch* b, int64_t periods, double* energy_out, double* no
 int sv_batch_forms(const sv_batch* b, int* form_out) {
   if (!b || !form_out) return SV_EINVAL;
   for (int c = 0; c < b->n; ++c) form_out[c] = b->form[c];
+  return SV_OK;
+}
+
+int sv_batch_widths(const sv_batch* b, int* n_out) {
+  if (!b || !n_out) return SV_EINVAL;
+  for (int c = 0; c < b->n; ++c) n_out[c] = b->width[c];
   return SV_OK;
 }
 

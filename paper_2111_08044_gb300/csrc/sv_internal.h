@@ -27,9 +27,11 @@ struct sv_ctx;
 namespace fsv {
 
 // Batch-executor hooks into a context (sv_api.cu).
-// One period of the built evolution captured as a graph template (the
-// caller destroys it); the graph advances the device period counter.
-int ctx_capture_period(sv_ctx* ctx, cudaGraph_t* out);
+// A run of `periods` periods captured as one graph template (the caller
+// destroys it): for a block plan whose periods start off site 0, the
+// relabel into the period layout, the periods, and the last period's
+// hand-back to the natural layout.
+int ctx_capture_run(sv_ctx* ctx, int64_t periods, cudaGraph_t* out);
 // Account for periods run through such graphs on the host mirror.
 void ctx_advance(sv_ctx* ctx, int64_t periods);
 // Block passes of later builds keep at least `tiles` tiles per CTA.
@@ -125,6 +127,17 @@ struct BlockPass {
   std::vector<int> x_sites;   // sites whose <X> this pass measures
   bool diag = false;          // this pass measures the diagonal terms and norm
 };
+// The multi-gate form's passes: each applies, gate by gate, every pending
+// gate of the period inside its window of w sites (the natural layout is
+// kept, so windows move freely); x_sites and diag as for BlockPass.
+struct MultiPass {
+  int lo = 0;
+  std::vector<int> gates;     // indices into the period's gate list, in order
+  std::vector<int> x_sites;
+  bool diag = false;
+};
+std::vector<MultiPass> multigate_plan(int L, const std::vector<Gate2> &gates, int w);
+
 // cyclic: the period may start (and end) at the window s <= 7 that needs the
 // fewest passes instead of at site 0 (passes[0].lo is the start).
 std::vector<BlockPass> fusion_plan(int L, const std::vector<Gate2> &gates, int n,

@@ -39,6 +39,27 @@ constexpr int kGateEntries = 32;
 template <typename R>
 constexpr bool kGateLo = sizeof(R) == 4;
 
+// Multi-gate pass (k_multigate.cu): a tile of 2^tb amplitudes, state bits
+// 0-3 and A..A+tb-5, in shared memory; the pass's gates applied one after
+// another on adjacent tile bits.
+constexpr int kMgTileBits = 13;
+constexpr int kMgWindow = kMgTileBits - 4;  // sites a pass's window spans (L > 13)
+constexpr int kMgMaxX = 16;
+struct MultiArgs {
+  int L = 0, tb = 0, A = 4;
+  int ngates = 0;
+  const int* gidx = nullptr;      // device: the pass's gates (indices into the period's list)
+  const int* gq = nullptr;        // device: tile bit of each gate's first site
+  const float2* gates = nullptr;  // gate tables, kGateEntries complex per gate
+  long long stride = 0;           // per-period table stride (0: one table)
+  const long long* counter = nullptr;
+  int nx = 0;                     // sites whose <X> this pass measures
+  int xq[kMgMaxX] = {};           // their tile bits
+  float xc[kMgMaxX] = {};         // their coefficients
+  int diag = 0;                   // the period's last pass: diagonal part and norm
+  EpiParams ep;                   // diagonal coefficients, renormalisation, partials
+};
+
 struct LaunchCfg {
   int num_sms = 148;
   // at least this many tiles per CTA in block passes (0: one wave over the
@@ -49,6 +70,12 @@ struct LaunchCfg {
 // Grid (blocks of 256 threads) used by the plain gate pass for this L and
 // bond; it is also the number of partial pairs the pass writes.
 int plain_gate_grid(int L, int bond, int precision, const LaunchCfg& cfg);
+// Multi-gate pass: grid (it is also the number of partial pairs a pass writes),
+// shared-memory opt-in (at build time, outside any capture) and launch.
+int multigate_grid(int L, const LaunchCfg& cfg);
+cudaError_t multigate_prepare();
+cudaError_t launch_multigate(const MultiArgs& ma, void* psi, const LaunchCfg& cfg,
+                             cudaStream_t s);
 
 // Apply one 4x4 gate on bond `bond` in place (store = 1) or only measure
 // (store = 0).  gate: 16 complex (float2 for C64, double2 for C128) at

@@ -298,6 +298,13 @@ class FloquetBatch:
                     "sv_batch_forms")
         return out
 
+    def widths(self) -> np.ndarray:
+        """Block width n of each chain's form (0 for non-block forms)."""
+        out = np.zeros(self.n, dtype=np.int32)
+        self._check(self._lib.sv_batch_widths(self._b, out.ctypes.data_as(capi._ip)),
+                    "sv_batch_widths")
+        return out
+
     def chain_state(self, c: int) -> np.ndarray:
         """Host copy of chain c's complex64 state."""
         self._torch.cuda.synchronize(self.device)

@@ -10,7 +10,7 @@ from paper_2111_08044_gb300 import capi, inputs
 pytestmark = pytest.mark.gpu
 
 FORMS = [capi.SV_BATCH_PLAIN, capi.SV_BATCH_BLOCK_SIMT, capi.SV_BATCH_BLOCK_TC,
-         capi.SV_BATCH_RESIDENT, capi.SV_BATCH_AUTO]
+         capi.SV_BATCH_RESIDENT, capi.SV_BATCH_MULTIGATE, capi.SV_BATCH_AUTO]
 
 
 def _chains(Ls, seed):
@@ -28,6 +28,7 @@ def test_batch_forms_match_oracle(svlib, form):
     P = 8
     with FloquetBatch(chains, form=form) as b:
         forms = b.forms()
+        widths = b.widths()
         e, n = b.evolve(P)
         states = [b.chain_state(c) for c in range(len(chains))]
     for c, cfg in enumerate(chains):
@@ -35,8 +36,14 @@ def test_batch_forms_match_oracle(svlib, form):
         if form >= 0:
             fits = {capi.SV_BATCH_PLAIN: True, capi.SV_BATCH_BLOCK_SIMT: cfg.L >= 6,
                     capi.SV_BATCH_BLOCK_TC: cfg.L >= 13,
-                    capi.SV_BATCH_RESIDENT: cfg.L <= 14}[form]
+                    capi.SV_BATCH_RESIDENT: cfg.L <= 14,
+                    capi.SV_BATCH_MULTIGATE: True}[form]
             assert forms[c] == (form if fits else capi.SV_BATCH_PLAIN)
+        # the block forms' width: 6 when forced, 5..7 when the autotuner chose
+        if forms[c] in (capi.SV_BATCH_BLOCK_TC, capi.SV_BATCH_BLOCK_SIMT):
+            assert widths[c] == 6 if form >= 0 else 5 <= widths[c] <= 7
+        else:
+            assert widths[c] == 0
         psi_o, _, e_o, n_o = orc.run_chain(cfg, periods=P)
         np.testing.assert_allclose(e[c], e_o, atol=1e-5, rtol=0, err_msg=f"chain {c} L={cfg.L}")
         np.testing.assert_allclose(n[c], n_o, atol=1e-5, rtol=0)

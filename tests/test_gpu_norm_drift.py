@@ -27,6 +27,7 @@ FORMS = {
     "plain": dict(mode=capi.SV_MODE_PLAIN),
     "block_simt": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_FP32),
     "block_tc": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_BF16X3),
+    "multigate": dict(mode=capi.SV_MODE_MULTIGATE),
 }
 
 

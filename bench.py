@@ -215,7 +215,8 @@ def _time_form(args, mode, steps, rank, world, local):
 def _e2e(args, steps, rank, local):
     """Public API end to end with host buffers: sv_init from host spinors,
     sv_build_floquet from host parameters, then one sv_evolve per period
-    reading the period's energy and norm back to the host."""
+    reading the period's energy and norm back to the host (with the state
+    kept in the period layout between calls, sv_set_layout_policy)."""
     import torch
 
     from paper_2111_08044_gb300 import capi, inputs
@@ -230,6 +231,9 @@ def _e2e(args, steps, rank, local):
     t0 = time.perf_counter()
     sim.init_product_state(spinors)
     sim.build(**kw)
+    # one period per call: keep the state in the plan's period layout between
+    # calls instead of relabelling it in and out every call
+    sim.keep_period_layout(True)
     for _ in range(steps):
         sim.evolve(1)
     torch.cuda.synchronize()

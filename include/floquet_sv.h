@@ -275,6 +275,23 @@ int sv_save(sv_ctx *ctx, const char *path);
 int sv_load(sv_ctx *ctx, const char *path);
 int sv_checkpoint_info(const char *path, int *L, int *precision, int64_t *period);
 
+/*
+ * Layout of the state between sv_evolve calls.  A block plan may start its
+ * periods at a window off site 0; an evolution then relabels the state into
+ * that window's layout first and its last period hands back the natural
+ * layout, one extra pass per call.  With keep_period_layout = 1 the state
+ * stays in the period layout after sv_evolve / sv_evolve_profiled (callers
+ * evolving one period per call save that pass); every call that reads the
+ * state (sv_get_state, sv_expect_energy, sv_energy_moments, the overlaps,
+ * sv_renormalize, sv_adjoint, sv_save) and sv_build_floquet bring it back to
+ * the natural layout first, and calls that write the state set it natural.
+ * Meanwhile the attached buffer, read directly, holds the amplitudes in the
+ * period layout (window of the plan's first pass on bits 0..n-1).
+ * keep_period_layout = 0 (the default) restores the natural layout at once.
+ * Errors: SV_EINVAL, SV_ECUDA.
+ */
+int sv_set_layout_policy(sv_ctx *ctx, int keep_period_layout);
+
 /* Periods applied since sv_init / sv_set_state / sv_load. */
 int64_t sv_period_counter(const sv_ctx *ctx);
 

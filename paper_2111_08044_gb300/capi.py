@@ -90,6 +90,7 @@ SIGNATURES = {
     "sv_get_state": ([_vp, _vp, _sz], _i32),
     "sv_set_state": ([_vp, _vp, _sz, _i64], _i32),
     "sv_save": ([_vp, ctypes.c_char_p], _i32),
+    "sv_set_layout_policy": ([_vp, _i32], _i32),
     "sv_load": ([_vp, ctypes.c_char_p], _i32),
     "sv_checkpoint_info": ([ctypes.c_char_p, _ip, _ip, ctypes.POINTER(_i64)], _i32),
     "sv_period_counter": ([_vp], _i64),

@@ -264,6 +264,13 @@ int block_build(int L, const std::vector<Gate2>& gates, const Observable& obs, i
       ops.push_back({-1, lo, nx});
       lo = nx;
     }
+    lo = bp->start;
+    while (lo != 0) {  // from the period layout back to the natural one
+      nx = step(lo, 0);
+      bp->seq_leave.push_back((int)ops.size());
+      ops.push_back({-1, lo, nx});
+      lo = nx;
+    }
   }
   const BlockPass identity_pass = [&]() {
     BlockPass ip;
@@ -476,6 +483,16 @@ cudaError_t block_enqueue_entry(BlockPlan* bp, void* psi, cudaStream_t s) {
   cudaError_t e = ensure_maps(bp, psi);
   if (e != cudaSuccess) return e;
   for (int k : bp->seq_entry) {
+    e = launch_pass(bp, k, psi, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t block_enqueue_leave(BlockPlan* bp, void* psi, cudaStream_t s) {
+  cudaError_t e = ensure_maps(bp, psi);
+  if (e != cudaSuccess) return e;
+  for (int k : bp->seq_leave) {
     e = launch_pass(bp, k, psi, s);
     if (e != cudaSuccess) return e;
   }

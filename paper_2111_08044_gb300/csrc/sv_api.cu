@@ -66,6 +66,11 @@ struct sv_ctx {
   cudaGraphExec_t graph_exit = nullptr;  // an evolution's last period (block plans
                                          // whose periods start off site 0)
   bool cyclic = true;  // block plans may start their periods off site 0
+  // Between evolve calls the state is in the natural layout unless the
+  // caller asked to keep the period layout (sv_set_layout_policy); then
+  // in_period_layout says whether it currently is in the plan's start layout.
+  bool keep_layout = false;
+  bool in_period_layout = false;
 
   int launches_per_period = 0;
   int passes_per_period = 0;
@@ -255,19 +260,35 @@ int ensure_graph(sv_ctx* ctx) {
   return SV_OK;
 }
 
-// Launch `count` periods, the first of an evolution when `first` (preceded
-// by the relabel steps into the period layout) and its last when `last`.
-int launch_periods(sv_ctx* ctx, int64_t count, bool first, bool last) {
+// Launch `count` periods; the state enters the period layout first if it is
+// not there, and `last` (the call's last periods) hands back the natural
+// layout unless the caller keeps the period layout between calls.
+int launch_periods(sv_ctx* ctx, int64_t count, bool last) {
   const bool off = off_natural(ctx);
-  if (first && off && count > 0) {
+  if (count <= 0) return SV_OK;
+  if (off && !ctx->in_period_layout) {
     cudaError_t e = fsv::block_enqueue_entry(ctx->block, ctx->state, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "relabel launch");
+    ctx->in_period_layout = true;
   }
   for (int64_t k = 0; k < count; ++k) {
-    const bool exit = off && last && k + 1 == count;
+    const bool exit = off && last && !ctx->keep_layout && k + 1 == count;
     SV_CUDA(cudaGraphLaunch(exit ? ctx->graph_exit : ctx->graph, ctx->stream), "graph launch");
+    if (exit) ctx->in_period_layout = false;
     ++ctx->counter;
   }
+  return SV_OK;
+}
+
+// Bring a state kept in the period layout back to the natural layout.
+int ensure_natural(sv_ctx* ctx) {
+  if (!ctx->in_period_layout) return SV_OK;
+  DeviceGuard dg(ctx->device);
+  if (ctx->block) {
+    cudaError_t e = fsv::block_enqueue_leave(ctx->block, ctx->state, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "relabel launch");
+  }
+  ctx->in_period_layout = false;
   return SV_OK;
 }
 
@@ -764,6 +785,7 @@ int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
 }
 
 int sv_attach_state(sv_ctx* ctx, void* dev_ptr, size_t bytes) {
+  if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!dev_ptr) return fail(ctx, SV_EINVAL, "null state pointer");
   if (reinterpret_cast<uintptr_t>(dev_ptr) % 256 != 0)
@@ -778,6 +800,7 @@ int sv_attach_state(sv_ctx* ctx, void* dev_ptr, size_t bytes) {
 }
 
 int sv_init(sv_ctx* ctx, int L, const double* product_state) {
+  if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
   const int lmax = ctx->precision == SV_C128 ? 33 : 34;
@@ -825,6 +848,10 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
   if (p->mode == SV_MODE_MULTIGATE && ctx->precision != SV_C64)
     return fail(ctx, SV_EUNSUPPORTED, "multi-gate mode needs SV_C64");
   DeviceGuard dg(ctx->device);
+  {
+    int rc = ensure_natural(ctx);  // the new plan starts from the natural layout
+    if (rc) return rc;
+  }
   free_build(ctx);
   ctx->params = *p;
   ctx->n_period_params = p->n_period_params;
@@ -934,7 +961,7 @@ int sv_evolve(sv_ctx* ctx, int64_t periods, double* energy_out, double* norm_out
   while (done < periods) {
     const int64_t chunk = std::min<int64_t>(periods - done, kRing);
     const int64_t c0 = ctx->counter;
-    rc = launch_periods(ctx, chunk, done == 0, done + chunk == periods);
+    rc = launch_periods(ctx, chunk, done + chunk == periods);
     if (rc) return rc;
     if (energy_out || norm_out) {
       rc = read_ring(ctx, c0, chunk, energy_out ? energy_out + done : nullptr,
@@ -966,12 +993,15 @@ int sv_evolve_profiled(sv_ctx* ctx, int64_t periods, double* energy_out, double*
     }
   const int64_t c0 = ctx->counter;
   rc = SV_OK;
-  if (periods > 0 && off_natural(ctx)) {
+  if (periods > 0 && off_natural(ctx) && !ctx->in_period_layout) {
     cudaError_t e = fsv::block_enqueue_entry(ctx->block, ctx->state, ctx->stream);
     if (e != cudaSuccess) rc = cuda_fail(ctx, e, "relabel launch");
+    else ctx->in_period_layout = true;
   }
   for (int64_t p = 0; p < periods && rc == SV_OK; ++p) {
-    rc = enqueue_period_profiled(ctx, ctx->stream, ev.data(), p + 1 == periods);
+    const bool exit = p + 1 == periods && !ctx->keep_layout;
+    rc = enqueue_period_profiled(ctx, ctx->stream, ev.data(), exit);
+    if (rc == SV_OK && exit && off_natural(ctx)) ctx->in_period_layout = false;
     if (rc) break;
     ++ctx->counter;
     if (rc == SV_OK) {
@@ -992,6 +1022,8 @@ int sv_evolve_profiled(sv_ctx* ctx, int64_t periods, double* energy_out, double*
 int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   DeviceGuard dg(ctx->device);
   if (ctx->obs.general) {
     double E = 0.0;
@@ -1005,6 +1037,8 @@ int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
 int sv_energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm2) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   DeviceGuard dg(ctx->device);
   return energy_moments(ctx, energy, sigma_e, norm2);
 }
@@ -1012,6 +1046,8 @@ int sv_energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm
 int sv_overlap_product(sv_ctx* ctx, const double* spinors, double* overlap_re,
                        double* overlap_im) {
   int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
   if (rc) return rc;
   if (!spinors) return fail(ctx, SV_EINVAL, "null spinors");
   return product_overlap(ctx, 1, spinors, overlap_re, overlap_im);
@@ -1021,12 +1057,15 @@ int sv_overlap_pairs(sv_ctx* ctx, const double* pair_states, double* overlap_re,
                      double* overlap_im) {
   int rc = check_ready(ctx, false);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   if (!pair_states) return fail(ctx, SV_EINVAL, "null pair_states");
   if (ctx->L % 2) return fail(ctx, SV_EINVAL, "pair states need an even L");
   return product_overlap(ctx, 2, pair_states, overlap_re, overlap_im);
 }
 
 int sv_init_pairs(sv_ctx* ctx, int L, const double* pair_states) {
+  if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
   const int lmax = ctx->precision == SV_C128 ? 33 : 34;
@@ -1069,6 +1108,8 @@ int sv_init_pairs(sv_ctx* ctx, int L, const double* pair_states) {
 int sv_renormalize(sv_ctx* ctx, double* norm2_before) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   DeviceGuard dg(ctx->device);
   double n2 = 0.0;
   rc = measure(ctx, nullptr, &n2);
@@ -1088,6 +1129,8 @@ int sv_renormalize(sv_ctx* ctx, double* norm2_before) {
 
 int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_density) {
   int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
   if (rc) return rc;
   if (ctx->params.mode != SV_MODE_PLAIN)
     return fail(ctx, SV_EUNSUPPORTED, "the adjoint needs SV_MODE_PLAIN");
@@ -1215,6 +1258,8 @@ int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_
 int sv_get_state(sv_ctx* ctx, void* host_dst, size_t bytes) {
   int rc = check_ready(ctx, false);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   const size_t need = amp_bytes(ctx->precision) << ctx->L;
   if (!host_dst || bytes < need) return fail(ctx, SV_EINVAL, "host buffer too small");
   DeviceGuard dg(ctx->device);
@@ -1229,6 +1274,7 @@ int record_norm(sv_ctx* ctx, int64_t period);
 }  // namespace
 
 int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period) {
+  if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   int rc = check_ready(ctx, false);
   if (rc) return rc;
   const size_t need = amp_bytes(ctx->precision) << ctx->L;
@@ -1284,6 +1330,8 @@ int record_norm(sv_ctx* ctx, int64_t period) {
 int sv_save(sv_ctx* ctx, const char* path) {
   int rc = check_ready(ctx, false);
   if (rc) return rc;
+  rc = ensure_natural(ctx);  // a state kept in the period layout
+  if (rc) return rc;
   if (!path) return fail(ctx, SV_EINVAL, "null path");
   DeviceGuard dg(ctx->device);
   fsv::CkptHeader h;
@@ -1318,6 +1366,7 @@ int sv_save(sv_ctx* ctx, const char* path) {
 }
 
 int sv_load(sv_ctx* ctx, const char* path) {
+  if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!path) return fail(ctx, SV_EINVAL, "null path");
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
@@ -1376,6 +1425,14 @@ int sv_load(sv_ctx* ctx, const char* path) {
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
   ctx->counter = h.period;
   return record_norm(ctx, h.period);
+}
+
+int sv_set_layout_policy(sv_ctx* ctx, int keep_period_layout) {
+  if (!ctx) return SV_EINVAL;
+  if (keep_period_layout != 0 && keep_period_layout != 1)
+    return fail(ctx, SV_EINVAL, "keep_period_layout must be 0 or 1");
+  ctx->keep_layout = keep_period_layout != 0;
+  return ctx->keep_layout ? SV_OK : ensure_natural(ctx);
 }
 
 int64_t sv_period_counter(const sv_ctx* ctx) { return ctx ? ctx->counter : -1; }

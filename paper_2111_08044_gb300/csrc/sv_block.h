@@ -71,6 +71,8 @@ struct BlockPlan {
   // evolution (its last pass writes the natural layout), and the relabel
   // steps from the natural layout to the start that begin an evolution
   std::vector<int> seq_cyc, seq_exit, seq_entry;
+  // relabel steps from the period layout back to the natural one (identity)
+  std::vector<int> seq_leave;
   bool tensor_cores = false;
   std::vector<BlockPass> passes;
   std::vector<PassArgs> args;
@@ -103,6 +105,8 @@ void block_set_renorm(BlockPlan* bp, const Renorm& rn);
 size_t block_upload_bytes(const BlockPlan* bp);
 // The relabel steps that begin an evolution (none when the start is 0).
 cudaError_t block_enqueue_entry(BlockPlan* bp, void* psi, cudaStream_t s);
+// The relabel steps from the period layout back to the natural one.
+cudaError_t block_enqueue_leave(BlockPlan* bp, void* psi, cudaStream_t s);
 // One period; `last`: the evolution's last period, which hands back the
 // natural layout.
 cudaError_t block_enqueue_period(BlockPlan* bp, void* psi, long long* counter, double* ring,

@@ -86,6 +86,13 @@ class FloquetSimulator:
                    "sv_evolve")
         return e[:periods], n[:periods]
 
+    def keep_period_layout(self, keep: bool = True):
+        """Between evolve calls keep the state in the block plan's period
+        layout (sv_set_layout_policy): saves one relabel pass per call; the
+        calls that read the state restore the natural layout first."""
+        capi.check(self._lib.sv_set_layout_policy(self._ctx, 1 if keep else 0), self._ctx,
+                   "sv_set_layout_policy")
+
     def save(self, path: str):
         """Checkpoint the state and the period counter (sv_save)."""
         capi.check(self._lib.sv_save(self._ctx, str(path).encode()), self._ctx, "sv_save")

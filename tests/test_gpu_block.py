@@ -104,3 +104,34 @@ def test_tensor_core_variants_match_oracle(svlib, L, first, ew, periods):
     assert err < 4e-6 * np.sqrt(cfg.periods * info[0]), err
     np.testing.assert_allclose(e, e_o, atol=2e-6, rtol=0)
     np.testing.assert_allclose(nn, n_o, atol=5e-6, rtol=0)
+
+
+@pytest.mark.parametrize("L", [16, 22])
+def test_kept_period_layout_matches_natural_layout(svlib, L):
+    """sv_set_layout_policy(1): one period per sv_evolve call with the state
+    kept in the plan's period layout between calls (no relabel pass per
+    call).  Energies, the measured energy and the final state (brought back
+    to the natural layout by the state copy) agree with evolving in one
+    call; the only difference is one more rounding by a relabel pass."""
+    from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
+    cfg = inputs.ChainConfig(L=L, seed=40 + L)
+    kw = chain_params(cfg, mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_BF16X3)
+    P = 6
+    with FloquetSimulator(L) as sim:
+        sim.init_product_state(cfg.spinors())
+        sim.build(**kw)
+        e_ref, n_ref = sim.evolve(P)
+        psi_ref = sim.host_state()
+    with FloquetSimulator(L) as sim:
+        sim.init_product_state(cfg.spinors())
+        sim.build(**kw)
+        sim.keep_period_layout(True)
+        e = np.concatenate([sim.evolve(1)[0] for _ in range(P)])
+        e_meas, _ = sim.energy()        # restores the natural layout first
+        psi = sim.host_state()
+        e_more, _ = sim.evolve(2)       # and evolves on from there
+    np.testing.assert_allclose(e, e_ref, atol=1e-7, rtol=0)
+    assert abs(e_meas - e_ref[-1]) < 1e-6
+    err = np.linalg.norm(psi.astype(np.complex128) - psi_ref.astype(np.complex128))
+    assert err < 1e-6, err
+    assert np.all(np.isfinite(e_more))

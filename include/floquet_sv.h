@@ -56,6 +56,12 @@ extern "C" {
 /* state precision */
 #define SV_C64 0  /* complex64 amplitudes, FP32 arithmetic, FP64 reductions */
 #define SV_C128 1 /* complex128 amplitudes, FP64 arithmetic (check mode) */
+#define SV_DF64 2 /* double-float check mode: each real number is an unevaluated
+                     sum hi + lo of two FP32 values (about 48 significant bits),
+                     16 bytes an amplitude (hi re, lo re, hi im, lo im), FP32
+                     arithmetic (error-free sums and FMA products); plain mode
+                     only.  Read and written as complex128 by sv_get_state /
+                     sv_set_state. */
 
 /* evolution form */
 #define SV_MODE_PLAIN 0 /* one kernel pass per two-qubit gate */
@@ -112,7 +118,9 @@ int sv_version(void);
 
 /*
  * Create a context on CUDA device `device` for amplitudes of the given
- * precision (SV_C64 or SV_C128).  `cuda_stream` is a cudaStream_t (NULL:
+ * precision (SV_C64, SV_C128 or SV_DF64; SV_DF64 contexts have no
+ * sv_energy_moments, overlaps, sv_init_pairs, sv_adjoint, nor measurement of
+ * general chains: those return SV_EUNSUPPORTED).  `cuda_stream` is a cudaStream_t (NULL:
  * the legacy default stream).  *out receives the handle; free it with
  * sv_destroy.  Errors: SV_EINVAL (bad precision / null out), SV_ECUDA (no
  * such device), SV_ENOMEM.
@@ -121,7 +129,7 @@ int sv_create(sv_ctx **out, int device, int precision, void *cuda_stream);
 
 /*
  * Attach the caller's device buffer that holds the state: at least
- * 8*2^L bytes (SV_C64) or 16*2^L bytes (SV_C128), 256-byte aligned,
+ * 8*2^L bytes (SV_C64) or 16*2^L bytes (SV_C128, SV_DF64), 256-byte aligned,
  * interleaved (re, im).  The caller keeps ownership and must keep it alive
  * while the context uses it.  Errors: SV_EINVAL (null or misaligned).
  */
@@ -132,7 +140,7 @@ int sv_attach_state(sv_ctx *ctx, void *dev_ptr, size_t bytes);
  * state, cf. Eq. 9) into the attached buffer.  product_state: host array of
  * 4*L doubles, per site (re a, im a, re b, im b) with a the |0> and b the
  * |1> component; the library normalises each site.  Resets the period
- * counter to 0.  L: 2..34 (SV_C64), 2..33 (SV_C128).  Errors: SV_EINVAL
+ * counter to 0.  L: 2..34 (SV_C64), 2..33 (SV_C128, SV_DF64).  Errors: SV_EINVAL
  * (L out of range, buffer too small, zero spinor), SV_ESTATE (no buffer).
  */
 int sv_init(sv_ctx *ctx, int L, const double *product_state);
@@ -238,12 +246,17 @@ int sv_renormalize(sv_ctx *ctx, double *norm2_before);
 int sv_adjoint(sv_ctx *ctx, double *grad_theta, double *grad_hx,
                double *energy_density);
 
-/* Copy the state to host memory (bytes >= state size).  Errors: SV_EINVAL,
- * SV_ESTATE, SV_ECUDA. */
+/* Copy the state, natural layout, to `host_dst`: host memory or device
+ * memory of the context's device (bytes >= state size).  SV_C64 and SV_C128
+ * copy the amplitudes as held; SV_DF64 writes complex128 (hi + lo, exact in
+ * FP64), converted on the device through a 64 MiB buffer the call
+ * allocates.  Errors: SV_EINVAL, SV_ESTATE, SV_ECUDA. */
 int sv_get_state(sv_ctx *ctx, void *host_dst, size_t bytes);
 
 /* Copy a state from host memory into the attached buffer (for checkpoint
- * resume); sets the period counter.  Errors as sv_get_state. */
+ * resume); sets the period counter.  SV_DF64 reads complex128 and keeps
+ * each part as the nearest float plus the nearest float to the remainder
+ * (relative error at most 2^-48).  Errors as sv_get_state. */
 int sv_set_state(sv_ctx *ctx, const void *host_src, size_t bytes, int64_t period);
 
 /*
@@ -252,7 +265,8 @@ int sv_set_state(sv_ctx *ctx, const void *host_src, size_t bytes, int64_t period
  * little-endian: bytes 0-7 "FLQSVCK1"; int32 L; int32 precision; int64
  * period counter; uint64 payload bytes; uint64 checksum of the payload;
  * uint64 checksum of bytes 0-39; then the 2^L amplitudes in the natural
- * layout (interleaved re, im, complex64 or complex128).  Checksums:
+ * layout (interleaved re, im, complex64 or complex128; SV_DF64: the
+ * double-float words as held, hi re, lo re, hi im, lo im).  Checksums:
  * FNV-1a (64-bit basis and prime) over little-endian 64-bit words.
  *
  * sv_save writes the attached state (stream-ordered after earlier calls)

@@ -1,8 +1,12 @@
 """Error accumulation of the complex64 forms over many periods.
 
-The complex64 plain and tensor-core block forms run in lockstep with the
-complex128 check mode; that reference is the same circuit in FP64 and
-agrees with the FP64 CPU oracle to 1e-11 wherever the oracle can run.
+The complex64 plain and tensor-core block forms run in lockstep with a
+check run of the same circuit: the complex128 mode (FP64 arithmetic) or the
+double-float mode df64 (FP32 pairs, about 48 significant bits), which gives
+the same reference about four times faster on a GPU whose FP64 rate is a
+small fraction of its FP32 rate.  Both agree with the FP64 CPU oracle to
+1e-11 wherever the oracle can run, and with each other to about 1e-12 over
+thousands of periods (compare them with `--ref df64 --forms c128`).
 
 Every `every` periods the study records, for each complex64 form:
 - the largest energy-density error over the chunk;
@@ -13,6 +17,7 @@ The infidelity is computed on the device in FP64. This mirrors the paper's
 accuracy study of long f32 runs against a reference (Sec. V).
 
     python -m paper_2111_08044_gb300.accuracy --L 26 --periods 1000 --every 100
+    python -m paper_2111_08044_gb300.accuracy --ref df64 --L 30 --periods 1000
 
 The echo mode follows the paper's own accuracy check (Sec. V) instead: from
 the product state, P periods forward and P inverse periods back in one form,
@@ -41,37 +46,48 @@ FORMS = {
     "block_tc": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_BF16X3),
     "block_simt": dict(mode=capi.SV_MODE_BLOCK, block_n=6, split=capi.SV_SPLIT_FP32),
 }
+# check modes, which a study may also compare with its reference
+CHECK = ("c128", "df64")
 
 
 def _infidelity(ref, psi):
     import torch
-    a = ref.state
-    b = psi.state.to(torch.complex128)
+    a = ref.state_c128()
+    b = psi.state_c128()
     ov = torch.vdot(a, b)
     na = torch.vdot(a, a).real
     nb = torch.vdot(b, b).real
     return float(1.0 - (ov.abs() ** 2) / (na * nb))
 
 
-def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc")):
+def study(L=26, periods=1000, every=100, seed=1, forms=("plain", "block_tc"), ref="c128"):
     """Rows of the study, one per `every` periods (a generator: each row is
-    available as soon as its periods have run)."""
+    available as soon as its periods have run).  `ref` is the check mode
+    (c128 or df64); `forms` are complex64 forms or the other check mode."""
+    import time
+    import torch
     cfg = inputs.ChainConfig(L=L, seed=seed)
-    ref = FloquetSimulator(L, precision="c128")
+    refname = ref
+    ref = FloquetSimulator(L, precision=refname)
     ref.init_product_state(cfg.spinors())
     ref.build(**chain_params(cfg))
     sims = {}
     for name in forms:
-        s = FloquetSimulator(L)
+        s = FloquetSimulator(L, precision=name if name in CHECK else "c64")
         s.init_product_state(cfg.spinors())
-        s.build(**chain_params(cfg, **FORMS[name]))
+        s.build(**chain_params(cfg, **FORMS.get(name, {})))
         sims[name] = s
+    t_ref = 0.0
     done = 0
     while done < periods:
         k = min(every, periods - done)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e_ref, n_ref = ref.evolve(k)
+        t_ref += time.perf_counter() - t0
         done += k
-        row = {"period": done, "energy_ref": float(e_ref[-1]), "norm_ref_dev": float(n_ref[-1] - 1)}
+        row = {"period": done, "ref": refname, "energy_ref": float(e_ref[-1]),
+               "norm_ref_dev": float(n_ref[-1] - 1), "ref_s_per_period": t_ref / done}
         for name, s in sims.items():
             e, n = s.evolve(k)
             row[name] = {"max_abs_energy_err": float(np.max(np.abs(e - e_ref))),
@@ -150,6 +166,7 @@ def main():
     ap.add_argument("--every", type=int, default=100)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--forms", default="plain,block_tc")
+    ap.add_argument("--ref", default="c128", choices=CHECK, help="check mode of the study")
     ap.add_argument("--echo", action="store_true")
     ap.add_argument("--circuit", action="store_true",
                     help="echo the paper's random circuit from its dimer state")
@@ -161,7 +178,7 @@ def main():
             for row in echo(a.L, ps, a.seed, form, circuit=a.circuit, omega=a.omega):
                 print(json.dumps(row), flush=True)
         return
-    for row in study(a.L, int(a.periods), a.every, a.seed, tuple(a.forms.split(","))):
+    for row in study(a.L, int(a.periods), a.every, a.seed, tuple(a.forms.split(",")), a.ref):
         print(json.dumps(row), flush=True)
 
 

@@ -23,6 +23,7 @@ SV_ESTATE = -5
 SV_EUNSUPPORTED = -6
 SV_C64 = 0
 SV_C128 = 1
+SV_DF64 = 2
 SV_MODE_PLAIN = 0
 SV_MODE_BLOCK = 1
 SV_MODE_MULTIGATE = 2

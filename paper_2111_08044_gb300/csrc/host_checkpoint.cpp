@@ -6,9 +6,10 @@
 // Layout, little-endian:
 //   bytes  0..7   magic "FLQSVCK1"
 //   bytes  8..11  int32  L
-//   bytes 12..15  int32  precision (SV_C64 or SV_C128)
+//   bytes 12..15  int32  precision (SV_C64, SV_C128 or SV_DF64)
 //   bytes 16..23  int64  period counter
 //   bytes 24..31  uint64 payload bytes (8 or 16 bytes x 2^L)
+//                 (SV_DF64: the double-float words as held on the device)
 //   bytes 32..39  uint64 checksum of the payload
 //   bytes 40..47  uint64 checksum of bytes 0..39
 //   bytes 48..    the amplitudes, natural layout (site i = bit i), (re, im)
@@ -68,10 +69,11 @@ bool ckpt_decode_header(const unsigned char in[kCkptHeaderBytes], CkptHeader* h)
   h->period = (int64_t)load_le64(in + 16);
   h->payload_bytes = load_le64(in + 24);
   h->payload_sum = load_le64(in + 32);
-  if (h->L < 2 || h->L > 34 || (h->precision != SV_C64 && h->precision != SV_C128)) return false;
-  if (h->precision == SV_C128 && h->L > 33) return false;
+  if (h->L < 2 || h->L > 34) return false;
+  if (h->precision != SV_C64 && h->precision != SV_C128 && h->precision != SV_DF64) return false;
+  if (h->precision != SV_C64 && h->L > 33) return false;
   if (h->period < 0) return false;
-  const uint64_t amp = h->precision == SV_C128 ? 16 : 8;
+  const uint64_t amp = h->precision == SV_C64 ? 8 : 16;
   return h->payload_bytes == (amp << h->L);
 }
 

@@ -471,6 +471,30 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename CT<R>::C* __restric
   }
 }
 
+// Double-float amplitudes to and from complex128 (state read-out and
+// write-in of SV_DF64; off the evolution path).  to_c128: hi + lo, exact in
+// FP64.  from_c128: hi = the nearest float, lo = the nearest float to the
+// remainder (relative error at most 2^-48).
+__global__ void __launch_bounds__(kThreads) k_df_to_c128(const dfc* __restrict__ src,
+                                                         double2* __restrict__ dst, uint64_t n) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const dfc v = src[x];
+    dst[x] = make_double2((double)v.x, (double)v.y);
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_c128_to_df(const double2* __restrict__ src,
+                                                         dfc* __restrict__ dst, uint64_t n) {
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    const double2 v = src[x];
+    dfc o;
+    o.x = df(v.x);
+    o.y = df(v.y);
+    dst[x] = o;
+  }
+}
+
 template <typename R>
 int gate_grid(int L, int bond, const LaunchCfg& cfg) {
   constexpr int LV = CT<R>::LV;
@@ -526,8 +550,9 @@ cudaError_t launch_gate_t(void* psi_, int L, int bond, const void* gate_base,
 }  // namespace
 
 int plain_gate_grid(int L, int bond, int precision, const LaunchCfg& cfg) {
-  return precision == SV_C128 ? gate_grid<double>(L, bond, cfg)
-                              : gate_grid<float>(L, bond, cfg);
+  if (precision == SV_C128) return gate_grid<double>(L, bond, cfg);
+  if (precision == SV_DF64) return gate_grid<df>(L, bond, cfg);
+  return gate_grid<float>(L, bond, cfg);
 }
 
 cudaError_t launch_plain_gate(int precision, void* psi, int L, int bond,
@@ -537,6 +562,9 @@ cudaError_t launch_plain_gate(int precision, void* psi, int L, int bond,
   if (precision == SV_C128)
     return launch_gate_t<double>(psi, L, bond, gate_base, period_stride, counter, ep,
                                  store, cfg, s);
+  if (precision == SV_DF64)
+    return launch_gate_t<df>(psi, L, bond, gate_base, period_stride, counter, ep, store, cfg,
+                             s);
   return launch_gate_t<float>(psi, L, bond, gate_base, period_stride, counter, ep, store,
                               cfg, s);
 }
@@ -553,6 +581,8 @@ cudaError_t launch_product_state(int precision, void* psi, int L, const double* 
   const int grid = cfg.num_sms * kBlocksPerSM;
   if (precision == SV_C128)
     k_product_state<double><<<grid, kThreads, 0, s>>>(static_cast<double2*>(psi), L, spinors);
+  else if (precision == SV_DF64)
+    k_product_state<df><<<grid, kThreads, 0, s>>>(static_cast<dfc*>(psi), L, spinors);
   else
     k_product_state<float><<<grid, kThreads, 0, s>>>(static_cast<float2*>(psi), L, spinors);
   return cudaGetLastError();
@@ -565,9 +595,23 @@ cudaError_t launch_renormalize(int precision, void* psi, int L, const double* ri
   if (precision == SV_C128)
     k_scale<double><<<grid, kThreads, 0, s>>>(static_cast<double2*>(psi), L, ring, ring_len,
                                               counter);
+  else if (precision == SV_DF64)
+    k_scale<df><<<grid, kThreads, 0, s>>>(static_cast<dfc*>(psi), L, ring, ring_len, counter);
   else
     k_scale<float><<<grid, kThreads, 0, s>>>(static_cast<float2*>(psi), L, ring, ring_len,
                                              counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_convert(const void* src, void* dst, uint64_t n, int to_c128,
+                              const LaunchCfg& cfg, cudaStream_t s) {
+  const int grid = cfg.num_sms * kBlocksPerSM;
+  if (to_c128)
+    k_df_to_c128<<<grid, kThreads, 0, s>>>(static_cast<const dfc*>(src),
+                                           static_cast<double2*>(dst), n);
+  else
+    k_c128_to_df<<<grid, kThreads, 0, s>>>(static_cast<const double2*>(src),
+                                           static_cast<dfc*>(dst), n);
   return cudaGetLastError();
 }
 

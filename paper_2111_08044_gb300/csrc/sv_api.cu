@@ -113,7 +113,7 @@ struct DeviceGuard {
   }
 };
 
-size_t amp_bytes(int precision) { return precision == SV_C128 ? 16 : 8; }
+size_t amp_bytes(int precision) { return precision == SV_C64 ? 8 : 16; }
 
 void drop_graph(sv_ctx* ctx) {
   if (ctx->graph) {
@@ -712,6 +712,21 @@ void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<float2>& out
   }
 }
 
+// double-float entries (re hi, re lo, im hi, im lo): hi the nearest float,
+// lo the nearest float to the remainder; zero residual entries
+float2 split_df(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<float4>& out, size_t at) {
+  for (size_t g = 0; g < gates.size(); ++g)
+    for (int k = 0; k < 16; ++k) {
+      const float2 re = split_df(gates[g].m[k].real()), im = split_df(gates[g].m[k].imag());
+      out[at + fsv::kGateEntries * g + k] = make_float4(re.x, re.y, im.x, im.y);
+      out[at + fsv::kGateEntries * g + 16 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<double2>& out, size_t at) {
   for (size_t g = 0; g < gates.size(); ++g)
     for (int k = 0; k < 16; ++k) {
@@ -719,6 +734,56 @@ void upload_gates(const std::vector<fsv::Gate2>& gates, std::vector<double2>& ou
           make_double2(gates[g].m[k].real(), gates[g].m[k].imag());
       out[at + fsv::kGateEntries * g + 16 + k] = make_double2(0.0, 0.0);
     }
+}
+
+// The gate tables of every period-parameter set, in the context's entry type.
+template <typename E>
+int upload_tables(sv_ctx* ctx, const sv_floquet_params& p, int64_t ntab, int ng) {
+  std::vector<E> tab((size_t)ntab * ng * fsv::kGateEntries);
+  for (int64_t k = 0; k < ntab; ++k) {
+    auto gk = k == 0 ? ctx->gates : fsv::period_gates(ctx->L, p, ctx->theta_p[k], ctx->hx_p[k]);
+    upload_gates(gk, tab, (size_t)k * ng * fsv::kGateEntries);
+  }
+  SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes, cudaMemcpyHostToDevice,
+                          ctx->stream),
+          "upload gates");
+  SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return SV_OK;
+}
+
+// SV_DF64 state read-out (to_host) or write-in as complex128 amplitudes,
+// through a device buffer of at most 64 MiB converted chunk by chunk.
+int df_transfer(sv_ctx* ctx, void* host, bool to_host) {
+  const uint64_t n = 1ull << ctx->L;
+  const uint64_t chunk = std::min<uint64_t>(n, (64ull << 20) / 16);
+  void* d_tmp = nullptr;
+  SV_CUDA(cudaMallocAsync(&d_tmp, chunk * 16, ctx->stream), "conversion buffer");
+  cudaError_t e = cudaSuccess;
+  char* h = static_cast<char*>(host);
+  char* st = static_cast<char*>(ctx->state);
+  for (uint64_t at = 0; at < n && e == cudaSuccess; at += chunk) {
+    const uint64_t m = std::min(chunk, n - at);
+    if (to_host) {
+      e = fsv::launch_df_convert(st + 16 * at, d_tmp, m, 1, ctx->cfg, ctx->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + 16 * at, d_tmp, 16 * m, cudaMemcpyDefault, ctx->stream);
+    } else {
+      e = cudaMemcpyAsync(d_tmp, h + 16 * at, 16 * m, cudaMemcpyDefault, ctx->stream);
+      if (e == cudaSuccess)
+        e = fsv::launch_df_convert(d_tmp, st + 16 * at, m, 0, ctx->cfg, ctx->stream);
+    }
+    // the host chunk and the buffer are reused by the next iteration
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  cudaFreeAsync(d_tmp, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "double-float state transfer");
+  return SV_OK;
+}
+
+// Calls that have no double-float kernels.
+int no_df(sv_ctx* ctx, const char* what) {
+  return fail(ctx, SV_EUNSUPPORTED, "%s needs SV_C64 or SV_C128", what);
 }
 
 }  // namespace
@@ -730,7 +795,7 @@ int sv_version(void) { return 1; }
 int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
   if (!out) return SV_EINVAL;
   *out = nullptr;
-  if (precision != SV_C64 && precision != SV_C128) return SV_EINVAL;
+  if (precision != SV_C64 && precision != SV_C128 && precision != SV_DF64) return SV_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -766,6 +831,10 @@ int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
     if (precision == SV_C128) {
       double2 id[fsv::kGateEntries] = {};  // identity, zero residual
       for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0;
+      ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
+    } else if (precision == SV_DF64) {
+      float4 id[fsv::kGateEntries] = {};  // (re hi, re lo, im hi, im lo)
+      for (int k = 0; k < 4; ++k) id[5 * k].x = 1.0f;
       ok = cudaMemcpy(ctx->d_ident, id, sizeof(id), cudaMemcpyHostToDevice) == cudaSuccess;
     } else {
       float2 id[fsv::kGateEntries] = {};
@@ -803,7 +872,7 @@ int sv_init(sv_ctx* ctx, int L, const double* product_state) {
   if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
-  const int lmax = ctx->precision == SV_C128 ? 33 : 34;
+  const int lmax = ctx->precision == SV_C64 ? 34 : 33;
   if (L < 2 || L > lmax) return fail(ctx, SV_EINVAL, "L=%d out of range 2..%d", L, lmax);
   if (!product_state) return fail(ctx, SV_EINVAL, "null product_state");
   if (ctx->state_bytes < (amp_bytes(ctx->precision) << L))
@@ -912,29 +981,11 @@ int sv_build_floquet(sv_ctx* ctx, const sv_floquet_params* p) {
       return fail(ctx, SV_ENOMEM, "partials allocation failed");
     }
     SV_CUDA(cudaMemsetAsync(ctx->d_part_evolve, 0, pbytes, ctx->stream), "memset partials");
-    if (ctx->precision == SV_C128) {
-      std::vector<double2> tab((size_t)ntab * ng * fsv::kGateEntries);
-      for (int64_t k = 0; k < ntab; ++k) {
-        auto gk = k == 0 ? ctx->gates
-                         : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
-        upload_gates(gk, tab, (size_t)k * ng * fsv::kGateEntries);
-      }
-      SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
-                              cudaMemcpyHostToDevice, ctx->stream),
-              "upload gates");
-      SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
-    } else {
-      std::vector<float2> tab((size_t)ntab * ng * fsv::kGateEntries);
-      for (int64_t k = 0; k < ntab; ++k) {
-        auto gk = k == 0 ? ctx->gates
-                         : fsv::period_gates(ctx->L, *p, ctx->theta_p[k], ctx->hx_p[k]);
-        upload_gates(gk, tab, (size_t)k * ng * fsv::kGateEntries);
-      }
-      SV_CUDA(cudaMemcpyAsync(ctx->d_gates, tab.data(), ctx->d_gates_bytes,
-                              cudaMemcpyHostToDevice, ctx->stream),
-              "upload gates");
-      SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
-    }
+    int urc = SV_OK;
+    if (ctx->precision == SV_C128) urc = upload_tables<double2>(ctx, *p, ntab, ng);
+    else if (ctx->precision == SV_DF64) urc = upload_tables<float4>(ctx, *p, ntab, ng);
+    else urc = upload_tables<float2>(ctx, *p, ntab, ng);
+    if (urc) return urc;
     ctx->passes_per_period = ng;
     ctx->launches_per_period = ng + 1;
     ctx->build_bytes = ctx->d_gates_bytes;
@@ -1026,6 +1077,7 @@ int sv_expect_energy(sv_ctx* ctx, double* energy_density, double* norm2) {
   if (rc) return rc;
   DeviceGuard dg(ctx->device);
   if (ctx->obs.general) {
+    if (ctx->precision == SV_DF64) return no_df(ctx, "measuring a general chain");
     double E = 0.0;
     rc = energy_moments(ctx, &E, nullptr, norm2);
     if (rc == SV_OK && energy_density) *energy_density = E / ctx->L;
@@ -1039,6 +1091,7 @@ int sv_energy_moments(sv_ctx* ctx, double* energy, double* sigma_e, double* norm
   if (rc) return rc;
   rc = ensure_natural(ctx);  // a state kept in the period layout
   if (rc) return rc;
+  if (ctx->precision == SV_DF64) return no_df(ctx, "sv_energy_moments");
   DeviceGuard dg(ctx->device);
   return energy_moments(ctx, energy, sigma_e, norm2);
 }
@@ -1050,6 +1103,7 @@ int sv_overlap_product(sv_ctx* ctx, const double* spinors, double* overlap_re,
   rc = ensure_natural(ctx);  // a state kept in the period layout
   if (rc) return rc;
   if (!spinors) return fail(ctx, SV_EINVAL, "null spinors");
+  if (ctx->precision == SV_DF64) return no_df(ctx, "sv_overlap_product");
   return product_overlap(ctx, 1, spinors, overlap_re, overlap_im);
 }
 
@@ -1061,6 +1115,7 @@ int sv_overlap_pairs(sv_ctx* ctx, const double* pair_states, double* overlap_re,
   if (rc) return rc;
   if (!pair_states) return fail(ctx, SV_EINVAL, "null pair_states");
   if (ctx->L % 2) return fail(ctx, SV_EINVAL, "pair states need an even L");
+  if (ctx->precision == SV_DF64) return no_df(ctx, "sv_overlap_pairs");
   return product_overlap(ctx, 2, pair_states, overlap_re, overlap_im);
 }
 
@@ -1068,7 +1123,8 @@ int sv_init_pairs(sv_ctx* ctx, int L, const double* pair_states) {
   if (ctx) ctx->in_period_layout = false;  // the state is (re)written in the natural layout
   if (!ctx) return SV_EINVAL;
   if (!ctx->state) return fail(ctx, SV_ESTATE, "no state buffer attached");
-  const int lmax = ctx->precision == SV_C128 ? 33 : 34;
+  if (ctx->precision == SV_DF64) return no_df(ctx, "sv_init_pairs");
+  const int lmax = ctx->precision == SV_C64 ? 34 : 33;
   if (L < 2 || L > lmax || L % 2)
     return fail(ctx, SV_EINVAL, "L=%d must be even and in 2..%d", L, lmax);
   if (!pair_states) return fail(ctx, SV_EINVAL, "null pair_states");
@@ -1132,6 +1188,7 @@ int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_
   if (rc) return rc;
   rc = ensure_natural(ctx);  // a state kept in the period layout
   if (rc) return rc;
+  if (ctx->precision == SV_DF64) return no_df(ctx, "sv_adjoint");
   if (ctx->params.mode != SV_MODE_PLAIN)
     return fail(ctx, SV_EUNSUPPORTED, "the adjoint needs SV_MODE_PLAIN");
   if (ctx->n_period_params <= 0)
@@ -1263,7 +1320,8 @@ int sv_get_state(sv_ctx* ctx, void* host_dst, size_t bytes) {
   const size_t need = amp_bytes(ctx->precision) << ctx->L;
   if (!host_dst || bytes < need) return fail(ctx, SV_EINVAL, "host buffer too small");
   DeviceGuard dg(ctx->device);
-  SV_CUDA(cudaMemcpyAsync(host_dst, ctx->state, need, cudaMemcpyDeviceToHost, ctx->stream),
+  if (ctx->precision == SV_DF64) return df_transfer(ctx, host_dst, true);
+  SV_CUDA(cudaMemcpyAsync(host_dst, ctx->state, need, cudaMemcpyDefault, ctx->stream),
           "copy state");
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");
   return SV_OK;
@@ -1282,8 +1340,13 @@ int sv_set_state(sv_ctx* ctx, const void* host_src, size_t bytes, int64_t period
   if (period < 0) return fail(ctx, SV_EINVAL, "period must be >= 0");
   DeviceGuard dg(ctx->device);
   long long c = period;
-  SV_CUDA(cudaMemcpyAsync(ctx->state, host_src, need, cudaMemcpyHostToDevice, ctx->stream),
-          "copy state");
+  if (ctx->precision == SV_DF64) {
+    rc = df_transfer(ctx, const_cast<void*>(host_src), false);
+    if (rc) return rc;
+  } else {
+    SV_CUDA(cudaMemcpyAsync(ctx->state, host_src, need, cudaMemcpyHostToDevice, ctx->stream),
+            "copy state");
+  }
   SV_CUDA(cudaMemcpyAsync(ctx->d_counter, &c, sizeof(c), cudaMemcpyHostToDevice, ctx->stream),
           "set counter");
   SV_CUDA(cudaStreamSynchronize(ctx->stream), "synchronize");

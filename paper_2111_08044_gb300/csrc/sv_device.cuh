@@ -29,6 +29,90 @@ struct CT<double> {
   static constexpr int LV = 0;
 };
 
+// Double-float real (SV_DF64): the unevaluated sum hi + lo of two FP32
+// numbers, |lo| <= ulp(hi) / 2, about 48 significant bits.  Built from the
+// error-free transformations of Dekker (1971) and Knuth: two_sum (the exact
+// rounding error of a + b), fast_two_sum (the same when |a| >= |b|) and
+// two_prod (the exact error of a * b, one FMA).  All steps use the _rn
+// intrinsics, so the compiler neither contracts nor reorders them.
+struct df {
+  float hi, lo;
+  df() = default;
+  __device__ __forceinline__ df(int v) : hi((float)v), lo(0.f) {}  // exact below 2^24
+  __device__ __forceinline__ df(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit df(double v) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+  }
+  __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) dfc {
+  df x, y;
+};
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// a + b: the exact sum of the leading parts, the trailing parts added to its
+// error, one renormalisation; absolute error about 2^-46 (|a| + |b|)
+__device__ __forceinline__ df operator+(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+// error of the product hi parts plus the cross terms (lo * lo dropped)
+__device__ __forceinline__ float prod_err(df a, df b, float p) {
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  return __fmaf_rn(a.lo, b.hi, e);
+}
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return fast_two_sum(p, prod_err(a, b, p));
+}
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
+__device__ __forceinline__ df& operator*=(df& a, df b) { return a = a * b; }
+// acc + a b + c d with one renormalisation: both products' leading parts
+// enter exact sums, every error term is collected in one FP32 number
+__device__ __forceinline__ df dot2_acc(df acc, df a, df b, df c, df d) {
+  const float p1 = __fmul_rn(a.hi, b.hi), p2 = __fmul_rn(c.hi, d.hi);
+  const float e1 = prod_err(a, b, p1), e2 = prod_err(c, d, p2);
+  const df s1 = two_sum(acc.hi, p1);
+  const df s2 = two_sum(s1.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(acc.lo, s1.lo), __fadd_rn(s2.lo, e1)), e2);
+  return fast_two_sum(s2.hi, lo);
+}
+
+template <>
+struct CT<df> {
+  using C = dfc;
+  using V = dfc;
+  static constexpr int NV = 1;
+  static constexpr int LV = 0;
+};
+
+__device__ __forceinline__ void unpack(const dfc& v, dfc a[1]) { a[0] = v; }
+__device__ __forceinline__ dfc pack(const dfc a[1]) { return a[0]; }
+__device__ __forceinline__ dfc cmac(dfc acc, dfc g, dfc v) {
+  acc.x = dot2_acc(acc.x, g.x, v.x, -g.y, v.y);
+  acc.y = dot2_acc(acc.y, g.x, v.y, g.y, v.x);
+  return acc;
+}
+__device__ __forceinline__ dfc shfl_xor(dfc v, int m) {
+  v.x.hi = __shfl_xor_sync(0xffffffffu, v.x.hi, m);
+  v.x.lo = __shfl_xor_sync(0xffffffffu, v.x.lo, m);
+  v.y.hi = __shfl_xor_sync(0xffffffffu, v.y.hi, m);
+  v.y.lo = __shfl_xor_sync(0xffffffffu, v.y.lo, m);
+  return v;
+}
+
 __device__ __forceinline__ void unpack(const float4& v, float2 a[2]) {
   a[0] = make_float2(v.x, v.y);
   a[1] = make_float2(v.z, v.w);

@@ -101,6 +101,10 @@ cudaError_t launch_product_state(int precision, void* psi, int L,
 cudaError_t launch_renormalize(int precision, void* psi, int L, const double* ring,
                                int ring_len, const long long* counter,
                                const LaunchCfg& cfg, cudaStream_t s);
+// SV_DF64 state <-> complex128 (n amplitudes; to_c128: src double-float,
+// dst complex128; else the reverse)
+cudaError_t launch_df_convert(const void* src, void* dst, uint64_t n, int to_c128,
+                              const LaunchCfg& cfg, cudaStream_t s);
 
 // Coefficients of H0 = J sum_b Z_b Z_{b+1} + sum_i cx[i] X_i + sum_i cz[i] Z_i
 // (L <= 34), passed by value to the adjoint seed kernel.

@@ -25,8 +25,13 @@ class FloquetSimulator:
         import torch
         self._torch = torch
         self.L = int(L)
-        self.precision = capi.SV_C128 if precision == "c128" else capi.SV_C64
-        dtype = torch.complex128 if self.precision == capi.SV_C128 else torch.complex64
+        # df64: double-float check mode; its buffer holds (hi, lo) FP32 pairs
+        # in complex128-sized elements, read out as complex128 by state_c128()
+        precisions = {"c64": capi.SV_C64, "c128": capi.SV_C128, "df64": capi.SV_DF64}
+        if precision not in precisions:
+            raise ValueError(f"precision must be one of {sorted(precisions)}")
+        self.precision = precisions[precision]
+        dtype = torch.complex64 if self.precision == capi.SV_C64 else torch.complex128
         self.device = torch.device("cuda", device)
         if state is None:
             state = torch.empty(1 << self.L, dtype=dtype, device=self.device)
@@ -163,15 +168,29 @@ class FloquetSimulator:
         sizes = [k.size for k in self._keep]
         return max(sizes) if sizes else 0
 
+    def state_c128(self):
+        """The state as a complex128 CUDA tensor: the buffer itself (c128) or
+        a copy converted by the library (df64, c64)."""
+        torch = self._torch
+        if self.precision == capi.SV_C128:
+            return self.state
+        if self.precision == capi.SV_C64:
+            return self.state.to(torch.complex128)
+        out = torch.empty(1 << self.L, dtype=torch.complex128, device=self.device)
+        capi.check(self._lib.sv_get_state(self._ctx, ctypes.c_void_p(out.data_ptr()),
+                                          out.numel() * out.element_size()),
+                   self._ctx, "sv_get_state")
+        return out
+
     def host_state(self) -> np.ndarray:
-        dt = np.complex128 if self.precision == capi.SV_C128 else np.complex64
+        dt = np.complex64 if self.precision == capi.SV_C64 else np.complex128
         out = np.empty(1 << self.L, dtype=dt)
         capi.check(self._lib.sv_get_state(self._ctx, ctypes.c_void_p(out.ctypes.data),
                                           out.nbytes), self._ctx, "sv_get_state")
         return out
 
     def set_host_state(self, psi: np.ndarray, period: int = 0):
-        dt = np.complex128 if self.precision == capi.SV_C128 else np.complex64
+        dt = np.complex64 if self.precision == capi.SV_C64 else np.complex128
         a = np.ascontiguousarray(psi, dtype=dt)
         capi.check(self._lib.sv_set_state(self._ctx, ctypes.c_void_p(a.ctypes.data), a.nbytes,
                                           int(period)), self._ctx, "sv_set_state")

@@ -42,7 +42,8 @@ def _info(svlib, path):
 
 def test_checkpoint_format_round_trip_on_host(svlib, tmp_path):
     rng = np.random.default_rng(5)
-    for L, prec, dtype in ((6, capi.SV_C64, np.complex64), (5, capi.SV_C128, np.complex128)):
+    for L, prec, dtype in ((6, capi.SV_C64, np.complex64), (5, capi.SV_C128, np.complex128),
+                           (4, capi.SV_DF64, np.complex128)):
         psi = (rng.standard_normal(1 << L) + 1j * rng.standard_normal(1 << L)).astype(dtype)
         p = tmp_path / f"ok{L}.ckpt"
         _write(p, L, prec, 1234, psi.tobytes())

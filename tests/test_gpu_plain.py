@@ -1,6 +1,7 @@
 """GPU parity of the plain (per-gate) form against the FP64 oracle, through
 the C ABI.  Tolerances: complex64 energy density <= 1e-5 absolute and state
-infidelity <= 1e-5 per 1000 periods; complex128 check mode 1e-11."""
+infidelity <= 1e-5 per 1000 periods; complex128 and double-float check
+modes 1e-11."""
 import numpy as np
 import pytest
 
@@ -22,7 +23,7 @@ def _infidelity(a, b):
     return 1.0 - abs(ov) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
 
 
-@pytest.mark.parametrize("precision,tol", [("c64", 1e-5), ("c128", 1e-11)])
+@pytest.mark.parametrize("precision,tol", [("c64", 1e-5), ("c128", 1e-11), ("df64", 1e-11)])
 def test_small_preset_100_periods(svlib, precision, tol):
     from paper_2111_08044_gb300.sim import chain_params
     cfg = inputs.preset("small")
@@ -48,7 +49,7 @@ CASES = [(L, fl, ew) for L in (2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 14)
 
 
 @pytest.mark.parametrize("L,first,ew", CASES)
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c128", "df64"])
 def test_state_after_three_periods(svlib, L, first, ew, precision):
     """Every kernel variant (tiny chain, low bonds with shuffles, high bonds)
     and both layer orders against the oracle, element by element."""
@@ -61,7 +62,9 @@ def test_state_after_three_periods(svlib, L, first, ew, precision):
         sim.build(**chain_params(cfg))
         e, n = sim.evolve(cfg.periods)
         psi = sim.host_state()
-    tol = 2e-6 if precision == "c64" else 1e-13
+    # df64: about 2^-47 of the terms per complex multiply-add, against the
+    # FP64 mode's 2^-53
+    tol = {"c64": 2e-6, "c128": 1e-13, "df64": 5e-13}[precision]
     err = np.linalg.norm(psi.astype(np.complex128) - psi_o)
     assert err < tol * 4, err
     etol = 2e-6 if precision == "c64" else 1e-12
@@ -69,7 +72,7 @@ def test_state_after_three_periods(svlib, L, first, ew, precision):
     np.testing.assert_allclose(n, n_o, atol=etol, rtol=0)
 
 
-@pytest.mark.parametrize("precision", ["c64", "c128"])
+@pytest.mark.parametrize("precision", ["c64", "c128", "df64"])
 def test_initial_state_and_energy(svlib, precision):
     cfg = inputs.ChainConfig(L=13, seed=9)
     psi_o = orc.product_state(cfg.spinors())
@@ -104,7 +107,8 @@ def test_renormalize_and_state_roundtrip(svlib):
         np.testing.assert_allclose(sim.host_state(), psi, atol=1e-6, rtol=0)
 
 
-def test_per_period_parameters(svlib):
+@pytest.mark.parametrize("precision", ["c128", "df64"])
+def test_per_period_parameters(svlib, precision):
     """Per-period kick angle and field (plain form) against the oracle."""
     from paper_2111_08044_gb300.sim import chain_params
     P = 6
@@ -112,7 +116,7 @@ def test_per_period_parameters(svlib):
     cfg = inputs.ChainConfig(L=9, periods=P, seed=5, theta_p=rng.uniform(0.1, 0.5, P),
                              hx_p=rng.uniform(0.6, 1.0, P))
     psi_o, _, e_o, _ = orc.run_chain(cfg)
-    with _sim(cfg.L, "c128") as sim:
+    with _sim(cfg.L, precision) as sim:
         sim.init_product_state(cfg.spinors())
         sim.build(**chain_params(cfg))
         e, _ = sim.evolve(P)

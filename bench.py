@@ -246,6 +246,47 @@ def _e2e(args, steps, rank, local):
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16}
 
 
+def _batch_hbm_bound_ms(chains, forms, widths, hbm_gbs, run=16):
+    """HBM-bound milliseconds per period of the batch: every chain's passes
+    of a period, plus its entry relabel once per graph run of `run` periods
+    when its plan starts off site 0, each moving 16 B x 2^L (read and write
+    of complex64) at the measured copy bandwidth.  Resident chains keep
+    their state in shared memory within a run and count nothing.  None when
+    a chain runs a form without a host plan view (multi-gate)."""
+    import ctypes
+
+    from paper_2111_08044_gb300 import capi
+    from paper_2111_08044_gb300.sim import chain_params
+    lib = capi.load()
+    cache, total = {}, 0.0
+    for c, cfg in enumerate(chains):
+        f, L = int(forms[c]), cfg.L
+        if f == capi.SV_BATCH_RESIDENT:
+            continue
+        key = (L, f, int(widths[c]))
+        if key not in cache:
+            if f in (capi.SV_BATCH_BLOCK_SIMT, capi.SV_BATCH_BLOCK_TC):
+                p, _keep = capi.make_params(**chain_params(cfg, mode=capi.SV_MODE_BLOCK,
+                                                           block_n=int(widths[c]) or 6))
+                cnt = ctypes.c_int(0)
+                capi.check(lib.sv_host_fusion_plan(L, ctypes.byref(p), int(widths[c]) or 6,
+                                                   ctypes.byref(cnt), None, None, None))
+                lo = (ctypes.c_int * cnt.value)()
+                capi.check(lib.sv_host_fusion_plan(L, ctypes.byref(p), int(widths[c]) or 6,
+                                                   ctypes.byref(cnt), lo, None, None))
+                cache[key] = cnt.value + (1.0 / run if lo[0] != 0 else 0.0)
+            elif f == capi.SV_BATCH_PLAIN:
+                p, _keep = capi.make_params(**chain_params(cfg))
+                cnt = ctypes.c_int(0)
+                capi.check(lib.sv_host_period_gates(L, ctypes.byref(p), ctypes.byref(cnt), None,
+                                                    None))
+                cache[key] = float(cnt.value)
+            else:
+                return None
+        total += cache[key] * 16.0 * (1 << L) / (hbm_gbs * 1e9)
+    return total * 1e3
+
+
 def _batch(args, local):
     """The 512-chain batch (L 14..22, per-chain couplings): chain-periods/s
     over args.batch_periods periods after a warm-up run of 16, with the
@@ -276,6 +317,9 @@ def _batch(args, local):
     b.close()
     del b
     torch.cuda.empty_cache()
+    hbm_gbs = _peaks()[0]
+    bound_ms = _batch_hbm_bound_ms(chains, forms, widths, hbm_gbs)
+    ms_period = ms / args.batch_periods
     names = {0: "plain", 1: "block_simt", 2: "block_tc", 3: "resident", 4: "multigate"}
     by_L = {}
     for L in sorted(set(Ls.tolist())):
@@ -292,6 +336,9 @@ def _batch(args, local):
         "forms": {names[k]: int((forms == k).sum()) for k in range(5) if (forms == k).any()},
         "form_by_L": by_L,
         "norm_max_dev": float(np.abs(n - 1.0).max()),
+        "ms_per_period": ms_period,
+        "hbm_bound_ms_per_period": bound_ms,
+        "hbm_bound_frac": bound_ms / ms_period if bound_ms else None,
     }
 
 

@@ -468,9 +468,11 @@ int sv_host_store_view(int L, const sv_floquet_params *p, int n, int pass, int *
  * plain, block or multi-gate forms.  One CUDA graph advances every chain by
  * a run of periods, the chains as independent branches (within a run a
  * chain's block periods may start off site 0; every run hands back the
- * natural layout).  An autotuner times the forms that fit each distinct L,
- * with their block widths and tile runs, on a few of its chains and keeps
- * the fastest (chain-periods per second).
+ * natural layout).  Tensor-core chains of one L run as a group: each pass
+ * of all of them is one launch over all their tiles, and each period's
+ * energy reduces are one launch.  An autotuner times the forms that fit
+ * each distinct L (the CUDA-core block form at its widths) on a few of its
+ * chains and keeps the fastest (chain-periods per second).
  */
 typedef struct sv_batch sv_batch;
 

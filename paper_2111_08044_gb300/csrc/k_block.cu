@@ -536,6 +536,178 @@ cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* cou
   return cudaEventRecord(ev[P + 1], s);
 }
 
+// ------------------------------------------------------------ chain groups
+
+struct BlockGroup {
+  std::vector<GroupMember> m;
+  std::vector<PassArgs> ops;        // structure of each pass, ntiles over the group
+  GroupChain* d_chains = nullptr;   // [passes][chains]
+  ReduceItem* d_reduce = nullptr;   // [chains]
+  double* d_part = nullptr;         // [chains][measuring slots][grid] (energy, norm) pairs
+  int nt_log2 = 0;
+  int grid = 0;
+};
+
+namespace {
+template <typename T, size_t N>
+bool same_array(const T (&x)[N], const T (&y)[N]) {
+  return std::memcmp(x, y, sizeof(x)) == 0;
+}
+bool same_pass(const PassArgs& x, const PassArgs& y) {
+  return x.L == y.L && x.n == y.n && x.R == y.R && x.a == y.a && x.lo == y.lo &&
+         x.ntiles == y.ntiles && x.x_mask == y.x_mask && x.diag == y.diag &&
+         x.diag_lo == y.diag_lo && same_array(x.diag_nb, y.diag_nb) &&
+         same_array(x.sigma, y.sigma) && same_array(x.rowvec, y.rowvec) &&
+         same_array(x.spos, y.spos) && same_array(x.ssig, y.ssig) && x.st_ndims == y.st_ndims &&
+         x.st_tlo_dim == y.st_tlo_dim && x.st_tlo_shift == y.st_tlo_shift &&
+         x.st_thi_dim == y.st_thi_dim && x.st_thi_shift == y.st_thi_shift &&
+         x.slot == y.slot && (x.partial == nullptr) == (y.partial == nullptr);
+}
+bool renorm_active(const PassArgs& pa) { return pa.ep.rn.ring && pa.ep.rn.every > 0; }
+}  // namespace
+
+bool block_same_structure(const BlockPlan* a, const BlockPlan* b) {
+  if (!a || !b || !a->tensor_cores || !b->tensor_cores) return false;
+  if (a->L != b->L || a->n != b->n || a->start != b->start || a->nslots != b->nslots ||
+      a->args.size() != b->args.size() || a->seq_cyc != b->seq_cyc ||
+      a->seq_exit != b->seq_exit || a->seq_entry != b->seq_entry || a->seq_leave != b->seq_leave)
+    return false;
+  for (size_t k = 0; k < a->args.size(); ++k)
+    if (!same_pass(a->args[k], b->args[k])) return false;
+  return true;
+}
+
+int block_group_build(const std::vector<GroupMember>& mem, int ring_len, const LaunchCfg& cfg,
+                      cudaStream_t s, BlockGroup** out, std::string* msg) {
+  *out = nullptr;
+  if (mem.empty()) return SV_EINVAL;
+  const BlockPlan* ref = mem[0].plan;
+  for (const GroupMember& x : mem) {
+    if (!block_same_structure(ref, x.plan)) {
+      *msg = "the chains' plans differ";
+      return SV_EINVAL;
+    }
+    for (const PassArgs& pa : x.plan->args)
+      if (renorm_active(pa)) {
+        *msg = "a group does not fold renormalisation";
+        return SV_EUNSUPPORTED;
+      }
+  }
+  const long long nt = ref->args[0].ntiles;
+  int lg = 0;
+  while ((1ll << lg) < nt) ++lg;
+  for (const PassArgs& pa : ref->args)
+    if (pa.ntiles != nt || (1ll << lg) != nt) {
+      *msg = "tile counts differ between passes";
+      return SV_EINVAL;
+    }
+  const size_t C = mem.size(), K = ref->args.size();
+  BlockGroup* g = new BlockGroup();
+  g->m = mem;
+  g->nt_log2 = lg;
+  g->grid = (int)std::min<long long>(cfg.num_sms, nt * (long long)C);
+  g->ops = ref->args;
+  for (PassArgs& pa : g->ops) {
+    pa.ntiles = nt * (long long)C;
+    pa.W = nullptr;        // per chain
+    pa.partial = nullptr;  // per chain
+  }
+  // partial sums: the chains' own buffers hold one pair per CTA of their
+  // own launches; a group launch has its own grid, so the group keeps a
+  // buffer of [chains][slots][grid] pairs (zero where a CTA meets no tile
+  // of the chain)
+  const int S = std::max(1, ref->nslots), G = g->grid;
+  const size_t part_pairs = C * (size_t)S * G;
+  std::vector<GroupChain> hc(K * C);
+  std::vector<uint8_t> maps(block_tc_map_bytes());
+  cudaError_t e = cudaMalloc(&g->d_part, sizeof(double) * 2 * part_pairs);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    block_group_free(g);
+    *msg = "group partials allocation";
+    return SV_ENOMEM;
+  }
+  for (size_t k = 0; k < K; ++k)
+    for (size_t c = 0; c < C; ++c) {
+      const PassArgs& pa = mem[c].plan->args[k];
+      GroupChain& gc = hc[k * C + c];
+      if (block_tc_make_map(pa, mem[c].psi, maps.data()) != SV_OK) {
+        block_group_free(g);
+        *msg = "tensor map";
+        return SV_ECUDA;
+      }
+      std::memcpy(gc.map_in, maps.data(), sizeof(gc.map_in));
+      std::memcpy(gc.map_out, maps.data() + sizeof(gc.map_in), sizeof(gc.map_out));
+      gc.W = pa.W;
+      gc.partial = pa.slot >= 0 ? g->d_part + 2 * ((c * S + pa.slot) * (size_t)G) : nullptr;
+      std::memcpy(gc.cx, pa.cx, sizeof(gc.cx));
+      std::memcpy(gc.diag_f, pa.diag_f, sizeof(gc.diag_f));
+      std::memcpy(gc.diag_lin0, pa.diag_lin0, sizeof(gc.diag_lin0));
+    }
+  std::vector<ReduceItem> red(C);
+  for (size_t c = 0; c < C; ++c) {
+    const BlockPlan* bp = mem[c].plan;
+    red[c].partials = g->d_part + 2 * (c * (size_t)S * G);
+    red[c].n = (long long)S * G;
+    red[c].ring = mem[c].ring;
+    red[c].counter = mem[c].counter;
+    red[c].L = bp->L;
+    red[c].ring_len = ring_len;
+  }
+  e = cudaMalloc(&g->d_chains, sizeof(GroupChain) * hc.size());
+  if (e == cudaSuccess) e = cudaMalloc(&g->d_reduce, sizeof(ReduceItem) * C);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_part, 0, sizeof(double) * 2 * part_pairs, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->d_chains, hc.data(), sizeof(GroupChain) * hc.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->d_reduce, red.data(), sizeof(ReduceItem) * C, cudaMemcpyHostToDevice,
+                        s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays are freed below
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    block_group_free(g);
+    *msg = "group upload";
+    return SV_ECUDA;
+  }
+  *out = g;
+  return SV_OK;
+}
+
+int block_group_start(const BlockGroup* g) { return g->m[0].plan->start; }
+
+namespace {
+cudaError_t group_pass(BlockGroup* g, int k, cudaStream_t s) {
+  return launch_block_tc_group(g->ops[k], g->d_chains + (size_t)k * g->m.size(), g->nt_log2,
+                               g->m[0].plan->d_status, g->grid, s);
+}
+}  // namespace
+
+cudaError_t block_group_enqueue_entry(BlockGroup* g, cudaStream_t s) {
+  for (int k : g->m[0].plan->seq_entry) {
+    cudaError_t e = group_pass(g, k, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t block_group_enqueue_period(BlockGroup* g, cudaStream_t s, bool last) {
+  const BlockPlan* ref = g->m[0].plan;
+  for (int k : last ? ref->seq_exit : ref->seq_cyc) {
+    cudaError_t e = group_pass(g, k, s);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_period_reduce_many(g->d_reduce, (int)g->m.size(), s);
+}
+
+void block_group_free(BlockGroup* g) {
+  if (!g) return;
+  cudaFree(g->d_chains);
+  cudaFree(g->d_reduce);
+  cudaFree(g->d_part);
+  delete g;
+}
+
 void block_free(BlockPlan* bp) {
   if (!bp) return;
   cudaFree(bp->d_U);

@@ -115,9 +115,19 @@ enum : uint32_t {
   kBarMmaDone = 184,
   kTmemSlot = 192,
   kAbort = 196,
+  kBarWFree = 200,   // chain group: the MMAs are done with the operand block
   kRed = 256,        // 4 x 2 doubles
   kDiagQ = 512,      // 64 floats (to 768): window-window bond part of the diagonal
+  kGroupCoef = 768,  // chain group: cx[6], diag_f[5], diag_lin0[6] of the current chain
 };
+
+// A tensor map written by the host into global memory is read through the
+// tensormap proxy: acquire it before its first use.
+__device__ __forceinline__ void tensormap_acquire(const void* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                   reinterpret_cast<uint64_t>(map))
+               : "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -400,10 +410,19 @@ __device__ __forceinline__ int tile_row(const PassArgs& pa, int m) {
 // (small chains, many of them at once in a batch) all take the generic
 // instance (kGeneric, flags read at run time), so that SMs switching between
 // their CTAs keep one kernel's code in the instruction cache.
-template <bool kGeneric, bool kX, bool kDiag>
+//
+// kGroup (with kGeneric): one launch over the tiles of a chain group.  Tile
+// g of the group is tile g mod 2^nt_log2 of chain g / 2^nt_log2; a CTA takes
+// a contiguous range of them, so it meets each chain once.  At a change of
+// chain the producer reloads the operand block once the MMAs are done with
+// the previous one (kBarWFree), and the epilogue writes the previous chain's
+// partial sums and takes the new chain's coefficients and descriptors.
+template <bool kGeneric, bool kX, bool kDiag, bool kGroup = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_block_tc(const __grid_constant__ CUtensorMap tmap_in,
-               const __grid_constant__ CUtensorMap tmap_out, PassArgs pa, int* status) {
+               const __grid_constant__ CUtensorMap tmap_out, PassArgs pa, int* status,
+               const GroupChain* __restrict__ grp, int nt_log2) {
+  static_assert(!kGroup || kGeneric, "a group pass takes the generic epilogue");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -414,8 +433,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = pa.a;
   const long long ntiles = pa.ntiles;
+  // this CTA's tiles: strided over the pass, or (group) a contiguous range
+  const long long my_first = kGroup ? (long long)blockIdx.x * ntiles / gridDim.x : 0;
   const long long my_tiles =
-      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+      kGroup ? ((long long)blockIdx.x + 1) * ntiles / gridDim.x - my_first
+             : (blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  // tile index within its chain, and the chain, of this CTA's tile i
+  auto tile_of = [&](long long i) -> long long {
+    return kGroup ? ((my_first + i) & ((1ll << nt_log2) - 1)) : blockIdx.x + i * gridDim.x;
+  };
+  auto chain_of = [&](long long i) -> int { return kGroup ? (int)((my_first + i) >> nt_log2) : 0; };
+  // tile i starts a chain other than tile i - 1's
+  auto new_chain = [&](long long i) -> bool {
+    return kGroup && i > 0 && chain_of(i) != chain_of(i - 1);
+  };
 
   if (threadIdx.x == 0) {
     for (int b = 0; b < kSlots; ++b) {
@@ -430,6 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(mbase + kBarDFull, 1);
     mbar_init(mbase + kBarDFree, 128);
     mbar_init(mbase + kBarMmaDone, 1);
+    mbar_init(mbase + kBarWFree, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -582,7 +614,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     float* diag_q = reinterpret_cast<float*>(misc + kDiagQ);
     const bool do_x = kGeneric ? pa.x_mask != 0 : kX;
     const bool do_diag = kGeneric ? pa.diag != 0 : kDiag;
-    if (do_diag) {
+    // the measured coefficients: the pass's, or (group) the current chain's
+    float* gco = reinterpret_cast<float*>(misc + kGroupCoef);
+    auto CX = [&](int j) -> float {
+      if constexpr (kGroup) return gco[j];
+      else return pa.cx[j];
+    };
+    auto DF = [&](int k) -> float {
+      if constexpr (kGroup) return gco[6 + k];
+      else return pa.diag_f[k];
+    };
+    auto LIN0 = [&](int j) -> float {
+      if constexpr (kGroup) return gco[11 + j];
+      else return pa.diag_lin0[j];
+    };
+    if (!kGroup && do_diag) {
       if (r < kCols) {
         // window bits j and k are sites lo + j and lo + k: adjacent when
         // |j - k| = 1
@@ -598,7 +644,52 @@ __global__ void __launch_bounds__(kThreads, 1)
     // per-thread energy and norm over its tiles: compensated FP32 sums
     // (Kahan), so that no FP64 instruction runs per tile
     float es_s = 0.f, es_c = 0.f, ns_s = 0.f, ns_c = 0.f;
+    // energy partials of this CTA into part[2 blockIdx.x + {0, 1}] (fixed order)
+    auto flush = [&](double* part) {
+      if (!part) return;
+      double eacc = (double)es_s - (double)es_c, nacc = (double)ns_s - (double)ns_c;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+        nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
+      }
+      double* red = reinterpret_cast<double*>(misc + kRed);
+      if (lane == 0) {
+        red[2 * q] = eacc;
+        red[2 * q + 1] = nacc;
+      }
+      epilogue_sync();
+      if (q == 0 && lane == 0) {
+        part[2 * blockIdx.x] = (red[0] + red[2]) + (red[4] + red[6]);
+        part[2 * blockIdx.x + 1] = (red[1] + red[3]) + (red[5] + red[7]);
+      }
+    };
+    int cur = -1;  // group: the chain whose coefficients are loaded
+    const CUtensorMap* map_out = &tmap_out;
     for (long long i = 0; i < my_tiles; ++i) {
+      if constexpr (kGroup) {
+        const int c = chain_of(i);
+        if (c != cur) {
+          if (cur >= 0) {
+            flush(grp[cur].partial);
+            es_s = es_c = ns_s = ns_c = 0.f;
+          }
+          epilogue_sync();  // the previous chain's coefficients are no longer read
+          const GroupChain& gc = grp[c];
+          if (q == 0 && lane < 17)
+            gco[lane] = lane < 6 ? gc.cx[lane] : (lane < 11 ? gc.diag_f[lane - 6] : gc.diag_lin0[lane - 11]);
+          if (do_diag && r < kCols) {
+            float qv = 0.f;
+            for (int j = 0; j + 1 < kN; ++j)
+              if (((r >> j) & 1) && ((r >> (j + 1)) & 1)) qv += 4.f * gc.diag_f[0];
+            diag_q[r] = qv;
+          }
+          map_out = reinterpret_cast<const CUtensorMap*>(gc.map_out);
+          if (elected) tensormap_acquire(map_out);
+          epilogue_sync();
+          cur = c;
+        }
+      }
       const bool ok = wait_bar(mbase + kBarDFull, (uint32_t)(i & 1), abort, status);
       if (!epilogue_all_ok(ok)) break;  // the four epilogue warps leave together
       tc_fence_after();
@@ -657,10 +748,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             f2_split(xacc, lo, hi);
             sj = lo + hi;
           }
-          es += 2.f * pa.cx[j] * sj;
+          es += 2.f * CX(j) * sj;
         }
       }
-      const long long t = blockIdx.x + i * gridDim.x;
+      const long long t = tile_of(i);
       const uint32_t tlo = (uint32_t)(t & ((1ll << (a - kN)) - 1));
       const uint32_t thi = (uint32_t)(t >> (a - kN));
       if (do_diag) {
@@ -672,11 +763,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         // FP32 coefficients rounded on the host (no FP64 work per tile)
         Diag<float> dg;
         dg.L = pa.L;
-        dg.J = pa.diag_f[0];
-        dg.cz_bulk = pa.diag_f[1];
-        dg.cz_first = pa.diag_f[2];
-        dg.cz_last = pa.diag_f[3];
-        dg.czsum = pa.diag_f[4];
+        dg.J = DF(0);
+        dg.cz_bulk = DF(1);
+        dg.cz_first = DF(2);
+        dg.cz_last = DF(3);
+        dg.czsum = DF(4);
         dg.zzmask = (1ull << (pa.L - 1)) - 1;
         dg.bulkmask = ((1ull << pa.L) - 1) & ~1ull & ~(1ull << (pa.L - 1));
         const float h0 = dg(x0);
@@ -692,7 +783,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ps = pa.diag_nb[j][k];
             if (ps >= 0) nb += ((x0 >> ps) & 1) ? -1.f : 1.f;
           }
-          lin[j] = fmaf(-2.f * dg.J, nb, pa.diag_lin0[j]);
+          lin[j] = fmaf(-2.f * dg.J, nb, LIN0(j));
         }
         // h(x_c) = h0 + L(c) + Q[c] with L(c) = sum_j c_j lin_j.  The row is
         // taken in pairs (c, c + 1) = (2k, 2k + 1), k in Gray-code order, so
@@ -750,7 +841,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (elected) {
         if (pa.st_ndims == 3) {
           // the natural order: output bits 4-5, then the rows
-          tma_store_3d(&tmap_out, out_base, 0, (int)(tlo << 2), (int)(thi << 7));
+          tma_store_3d(map_out, out_base, 0, (int)(tlo << 2), (int)(thi << 7));
         } else {
           // the tile-index bits go to the store view's dimensions that their
           // state bits continue
@@ -759,33 +850,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                    (d == pa.st_thi_dim ? (int)(thi << pa.st_thi_shift) : 0);
           };
           if (pa.st_ndims == 4)
-            tma_store_4d(&tmap_out, out_base, 0, coord(1), coord(2), coord(3));
+            tma_store_4d(map_out, out_base, 0, coord(1), coord(2), coord(3));
           else
-            tma_store_5d(&tmap_out, out_base, 0, coord(1), coord(2), coord(3), coord(4));
+            tma_store_5d(map_out, out_base, 0, coord(1), coord(2), coord(3), coord(4));
         }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
     }
     // the CTA's stores complete before its shared memory is released
     if (elected) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    // energy partials of this CTA (fixed order)
-    if (pa.partial) {
-      double eacc = (double)es_s - (double)es_c, nacc = (double)ns_s - (double)ns_c;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
-        nacc += __shfl_xor_sync(0xffffffffu, nacc, o);
-      }
-      double* red = reinterpret_cast<double*>(misc + kRed);
-      if (lane == 0) {
-        red[2 * q] = eacc;
-        red[2 * q + 1] = nacc;
-      }
-      epilogue_sync();
-      if (q == 0 && lane == 0) {
-        pa.partial[2 * blockIdx.x] = (red[0] + red[2]) + (red[4] + red[6]);
-        pa.partial[2 * blockIdx.x + 1] = (red[1] + red[3]) + (red[5] + red[7]);
-      }
+    if constexpr (kGroup) {
+      if (cur >= 0) flush(grp[cur].partial);
+    } else {
+      flush(pa.partial);
     }
   } else {
     // ----------------------------------- MMA issue (warp 8), producer (warp 9)
@@ -803,7 +880,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n selp.u32 %0, 1, 0, e;\n}\n"
                    : "=r"(leader));
       bool ok = __all_sync(0xffffffffu, wait_bar(mbase + kBarW, 0, abort, status));
+      int wload = 0;  // group: operand blocks loaded after the first
       for (long long i = 0; i < my_tiles && ok; ++i) {
+        if (new_chain(i)) {
+          // the new chain's operand block
+          ++wload;
+          ok = __all_sync(0xffffffffu,
+                          wait_bar(mbase + kBarW, (uint32_t)(wload & 1), abort, status));
+          if (!ok) break;
+        }
 #pragma unroll 1
         for (int h = 0; h < 2 && ok; ++h) {
           // half h of tile i once its A digits are written and, for the first
@@ -830,6 +915,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           mma_commit(leader, mbase + kBarAFree + 8 * h);  // this half of A may be refilled
         }
         if (ok) mma_commit(leader, mbase + kBarDFull);
+        // the operand block may be replaced once this tile's MMAs are done
+        if (ok && i + 1 < my_tiles && new_chain(i + 1)) mma_commit(leader, mbase + kBarWFree);
       }
       // all issued MMAs complete before TMEM is released
       mma_commit(leader, mbase + kBarMmaDone);
@@ -838,20 +925,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else if (warp == 9 && lane == 0) {
       // load number g is box (g mod 4) of tile g / 4, into slot g mod kSlots
+      const CUtensorMap* map_in = &tmap_in;
       auto load_box = [&](long long g) {
-        const long long t = blockIdx.x + (g >> 2) * gridDim.x;
+        const long long t = tile_of(g >> 2);
         const int tlo = (int)(t & ((1ll << (a - kN)) - 1));
         const int thi = (int)(t >> (a - kN));
         const int slot = (int)(g % kSlots);
         const uint32_t bar = mbase + kBarFull + 8 * slot;
         mbar_expect_tx(bar, kBoxBytes);
-        tma_load_5d(sbase + kOffRing + slot * kBoxBytes, &tmap_in, bar, 0, (int)(g & 3), tlo, 0,
+        tma_load_5d(sbase + kOffRing + slot * kBoxBytes, map_in, bar, 0, (int)(g & 3), tlo, 0,
                     thi);
       };
-      mbar_expect_tx(mbase + kBarW, kWBytes);
-      const uint8_t* wsrc = static_cast<const uint8_t*>(pa.W);
-      for (int q = 0; q < 3; ++q)
-        bulk_load(w0 + q * (kWBytes / 3), wsrc + q * (kWBytes / 3), kWBytes / 3, mbase + kBarW);
+      auto load_w = [&](const void* src) {
+        mbar_expect_tx(mbase + kBarW, kWBytes);
+        const uint8_t* wsrc = static_cast<const uint8_t*>(src);
+        for (int q = 0; q < 3; ++q)
+          bulk_load(w0 + q * (kWBytes / 3), wsrc + q * (kWBytes / 3), kWBytes / 3,
+                    mbase + kBarW);
+      };
+      if constexpr (kGroup) {
+        map_in = reinterpret_cast<const CUtensorMap*>(grp[chain_of(0)].map_in);
+        tensormap_acquire(map_in);
+        load_w(grp[chain_of(0)].W);
+      } else {
+        load_w(pa.W);
+      }
+      int wload = 0;  // group: operand blocks loaded after the first
       const long long nloads = 4 * my_tiles;
       long long issued = 0;
       for (; issued < nloads; ++issued) {
@@ -860,6 +959,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             !wait_bar(mbase + kBarEmpty + 8 * (int)(issued % kSlots),
                       (uint32_t)((issued / kSlots - 1) & 1), abort, status))
           break;
+        if ((issued & 3) == 0 && new_chain(issued >> 2)) {
+          // a new chain: its descriptors, and its operand block once the
+          // MMAs of the previous chain are done
+          if (!wait_bar(mbase + kBarWFree, (uint32_t)(wload & 1), abort, status)) break;
+          const GroupChain& gc = grp[chain_of(issued >> 2)];
+          map_in = reinterpret_cast<const CUtensorMap*>(gc.map_in);
+          tensormap_acquire(map_in);
+          load_w(gc.W);
+          ++wload;
+        }
         load_box(issued);
       }
       if (*abort) {
@@ -872,7 +981,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         const long long t0 = clock64();
-        while (!mbar_try_wait(mbase + kBarW, 0) && clock64() - t0 < kTimeoutCycles) {
+        while (!mbar_try_wait(mbase + kBarW, (uint32_t)(wload & 1)) &&
+               clock64() - t0 < kTimeoutCycles) {
         }
       }
     }
@@ -1215,11 +1325,12 @@ int block_tc_make_map(const PassArgs& pa, void* psi, void* map_out) {
 size_t block_tc_map_bytes() { return 2 * sizeof(CUtensorMap); }
 
 cudaError_t block_tc_prepare() {
-  const void* fns[5] = {(const void*)k_block_tc<true, false, false>,
+  const void* fns[6] = {(const void*)k_block_tc<true, false, false>,
                         (const void*)k_block_tc<false, false, false>,
                         (const void*)k_block_tc<false, true, false>,
                         (const void*)k_block_tc<false, false, true>,
-                        (const void*)k_block_tc<false, true, true>};
+                        (const void*)k_block_tc<false, true, true>,
+                        (const void*)k_block_tc<true, false, false, true>};
   for (const void* f : fns) {
     const cudaError_t e =
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
@@ -1238,15 +1349,26 @@ cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int*
   const long long per_cta = (p.ntiles + grid - 1) / grid;
   const dim3 g(grid), b(kThreads);
   if (per_cta < kMinTilesSpecialised)
-    k_block_tc<true, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+    k_block_tc<true, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status, nullptr, 0);
   else if (p.diag && p.x_mask)
-    k_block_tc<false, true, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+    k_block_tc<false, true, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status, nullptr, 0);
   else if (p.diag)
-    k_block_tc<false, false, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+    k_block_tc<false, false, true><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status, nullptr, 0);
   else if (p.x_mask)
-    k_block_tc<false, true, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+    k_block_tc<false, true, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status, nullptr, 0);
   else
-    k_block_tc<false, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status);
+    k_block_tc<false, false, false><<<g, b, kSmemBytes, s>>>(maps[0], maps[1], p, status, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_tc_group(const PassArgs& pa, const GroupChain* chains, int nt_log2,
+                                  int* status, int grid, cudaStream_t s) {
+  // the kernel's descriptor parameters are unused: each chain's come from
+  // the group array
+  alignas(64) CUtensorMap unused[2];
+  std::memset(unused, 0, sizeof(unused));
+  k_block_tc<true, false, false, true><<<grid, kThreads, kSmemBytes, s>>>(
+      unused[0], unused[1], pa, status, chains, nt_log2);
   return cudaGetLastError();
 }
 

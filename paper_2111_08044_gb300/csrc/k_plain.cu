@@ -357,11 +357,9 @@ __global__ void __launch_bounds__(kThreads) k_gate_small(
 }
 
 // ------------------------------------------------------------- period reduce
-__global__ void __launch_bounds__(256) k_period_reduce(const double* __restrict__ partials,
-                                                       long long n, int L,
-                                                       double* __restrict__ ring,
-                                                       int ring_len, long long* counter,
-                                                       int advance) {
+__device__ void period_reduce_block(const double* __restrict__ partials, long long n, int L,
+                                    double* __restrict__ ring, int ring_len, long long* counter,
+                                    int advance) {
   __shared__ double se[256], sn[256];
   double e = 0.0, nn = 0.0;
   for (long long k = threadIdx.x; k < n; k += blockDim.x) {
@@ -386,6 +384,20 @@ __global__ void __launch_bounds__(256) k_period_reduce(const double* __restrict_
     ring[2 * slot + 1] = sn[0];
     if (advance) *counter = c + 1;
   }
+}
+
+__global__ void __launch_bounds__(256) k_period_reduce(const double* __restrict__ partials,
+                                                       long long n, int L,
+                                                       double* __restrict__ ring,
+                                                       int ring_len, long long* counter,
+                                                       int advance) {
+  period_reduce_block(partials, n, L, ring, ring_len, counter, advance);
+}
+
+// the period reduce of many chains, one block each
+__global__ void __launch_bounds__(256) k_period_reduce_many(const ReduceItem* __restrict__ items) {
+  const ReduceItem it = items[blockIdx.x];
+  period_reduce_block(it.partials, it.n, it.L, it.ring, it.ring_len, it.counter, 1);
 }
 
 // ------------------------------------------------------------ product state
@@ -573,6 +585,11 @@ cudaError_t launch_period_reduce(const double* partials, long long n, int L, dou
                                  int ring_len, long long* counter, int advance,
                                  cudaStream_t s) {
   k_period_reduce<<<1, 256, 0, s>>>(partials, n, L, ring, ring_len, counter, advance);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_period_reduce_many(const ReduceItem* items, int count, cudaStream_t s) {
+  k_period_reduce_many<<<count, 256, 0, s>>>(items);
   return cudaGetLastError();
 }
 

@@ -335,6 +335,18 @@ int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double*
 
 int ctx_ring_len() { return kRing; }
 
+int ctx_block_member(sv_ctx* ctx, BlockPlan** plan, void** psi, long long** counter,
+                     double** ring) {
+  if (!ctx || !ctx->built || ctx->params.mode != SV_MODE_BLOCK || !ctx->block ||
+      !ctx->block->tensor_cores)
+    return SV_ESTATE;
+  *plan = ctx->block;
+  *psi = ctx->state;
+  *counter = ctx->d_counter;
+  *ring = ctx->d_ring;
+  return SV_OK;
+}
+
 namespace {
 double unitarity_defect(const double* re, const double* im) {
   double d = 0.0, tr = 0.0;

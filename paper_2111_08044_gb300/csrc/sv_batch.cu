@@ -6,18 +6,19 @@
 // for the plain, block and multi-gate forms, for its evolution graph.  Chains of at most
 // 14 sites may instead run the resident form (k_batch.cu): one launch
 // advances all of them, each in one CTA's shared memory.  An evolution is
-// one CUDA graph per run of M periods: the resident launch and, for every
-// other chain, its run of M periods captured from its context (a block plan
-// whose periods start off site 0 relabels into its period layout at the
-// start of the run and hands back the natural layout at its end), the
-// chains as independent branches.
+// one CUDA graph per run of M periods: the resident launch; one branch per
+// group of tensor-core chains whose plans share their structure (same L),
+// each pass of all its chains one launch over all their tiles and each
+// period's reduces one launch; and, for every other chain, its run of M
+// periods captured from its context.  A block plan whose periods start off
+// site 0 relabels into its period layout at the start of the run and hands
+// back the natural layout at its end.
 //
 // The autotuner (form SV_BATCH_AUTO) times every form that fits a distinct
 // L, run together for four periods through the same kind of graph (the
-// tensor-core block form with 4, 8 or 16 tiles per CTA at least, the
-// CUDA-core block form at widths n = 5, 6 and 7, the plain, multi-gate and
-// resident forms), and keeps the fastest (most chain-periods per second)
-// for all chains of that L.  The resident form is
+// CUDA-core block form at widths n = 5, 6 and 7, the tensor-core block form
+// as a group, the plain, multi-gate and resident forms), and keeps the
+// fastest (most chain-periods per second) for all chains of that L.  The resident form is
 // timed on all chains of that L (one CTA each, so its rate grows with their
 // number); the others, which fill the device with one chain, on up to eight.
 #include <cuda_runtime.h>
@@ -32,6 +33,7 @@
 #include <vector>
 
 #include "sv_batch.h"
+#include "sv_block.h"
 
 struct sv_batch {
   int device = 0;
@@ -57,6 +59,7 @@ struct sv_batch {
   int res_maxL = 0;
   // graphs of one period and of M periods of every chain
   cudaGraphExec_t g1 = nullptr, gm = nullptr;
+  std::vector<fsv::BlockGroup*> groups;  // chain groups the two graphs launch
   int M = 16;
   int64_t counter = 0;
   std::string err;
@@ -65,10 +68,8 @@ struct sv_batch {
 namespace {
 
 constexpr size_t kAlign = 256;
-// Block passes of a batch share the device with other chains' passes: each
-// CTA keeps a run of tiles long enough to fill its pipeline.  The
-// autotuner picks the run length per L among these.
-constexpr int kTileRuns[3] = {4, 8, 16};
+// CUDA-core block passes of a batch share the device with other chains'
+// passes: each CTA keeps a run of at least this many tiles.
 constexpr int kDefaultTileRun = 8;
 constexpr int kSimtWidths[3] = {5, 6, 7};
 constexpr int kDefaultWidth = 6;
@@ -210,10 +211,47 @@ int build_graph_form(sv_batch* b, int c, int form, int min_tiles, int n) {
   return SV_OK;
 }
 
+// Tensor-core chains grouped by plan structure (an existing group of the
+// same structure is reused); the other chains are returned in `rest`.
+int make_groups(sv_batch* b, const std::vector<int>& chains, std::vector<int>* rest,
+                std::vector<fsv::BlockGroup*>* groups) {
+  std::vector<std::vector<fsv::GroupMember>> parts;
+  for (int c : chains) {
+    fsv::GroupMember m;
+    if (fsv::ctx_block_member(b->ctx[c], &m.plan, &m.psi, &m.counter, &m.ring) != SV_OK) {
+      rest->push_back(c);
+      continue;
+    }
+    bool placed = false;
+    for (auto& p : parts)
+      if (fsv::block_same_structure(p[0].plan, m.plan)) {
+        p.push_back(m);
+        placed = true;
+        break;
+      }
+    if (!placed) parts.push_back({m});
+  }
+  for (auto& p : parts) {
+    fsv::BlockGroup* g = nullptr;
+    std::string msg;
+    int rc = fsv::block_group_build(p, fsv::ctx_ring_len(), p[0].plan->cfg, b->stream, &g, &msg);
+    if (rc) return bfail(b, rc, "chain group: %s", msg.c_str());
+    groups->push_back(g);
+  }
+  return SV_OK;
+}
+
+void free_groups(std::vector<fsv::BlockGroup*>* groups) {
+  for (fsv::BlockGroup* g : *groups) fsv::block_group_free(g);
+  groups->clear();
+}
+
 // One graph advancing `periods` periods of the given graph-form chains and
-// of the resident set (if any).
+// of the resident set (if any).  Tensor-core chains run in groups, built on
+// the first call (groups empty) and reused by later ones; the caller frees
+// them after the graphs.
 int make_graph(sv_batch* b, const std::vector<int>& chains, const ResidentSet* rs, int periods,
-               cudaGraphExec_t* out) {
+               cudaGraphExec_t* out, std::vector<fsv::BlockGroup*>* groups) {
   *out = nullptr;
   cudaGraph_t g = nullptr;
   BCUDA(cudaGraphCreate(&g, 0), "graph create");
@@ -240,7 +278,40 @@ int make_graph(sv_batch* b, const std::vector<int>& chains, const ResidentSet* r
     if (e != cudaSuccess)
       return fail_g(bfail(b, SV_ECUDA, "resident node: %s", cudaGetErrorString(e)));
   }
-  for (int c : chains) {
+  std::vector<int> rest;
+  if (groups->empty()) {
+    int rc = make_groups(b, chains, &rest, groups);
+    if (rc) return fail_g(rc);
+  } else {
+    for (int c : chains) {
+      fsv::GroupMember m;
+      if (fsv::ctx_block_member(b->ctx[c], &m.plan, &m.psi, &m.counter, &m.ring) != SV_OK)
+        rest.push_back(c);
+    }
+  }
+  for (fsv::BlockGroup* grp : *groups) {
+    cudaGraph_t pg = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeRelaxed);
+    cudaError_t le = cudaSuccess;
+    if (e == cudaSuccess) {
+      if (periods > 0 && fsv::block_group_start(grp) != 0)
+        le = fsv::block_group_enqueue_entry(grp, b->cap_stream);
+      for (int k = 0; k < periods && le == cudaSuccess; ++k)
+        le = fsv::block_group_enqueue_period(grp, b->cap_stream, k + 1 == periods);
+      e = cudaStreamEndCapture(b->cap_stream, &pg);
+      if (le != cudaSuccess) e = le;
+    }
+    if (e != cudaSuccess) {
+      if (pg) cudaGraphDestroy(pg);
+      return fail_g(bfail(b, SV_ECUDA, "group capture: %s", cudaGetErrorString(e)));
+    }
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, pg);
+    cudaGraphDestroy(pg);
+    if (e != cudaSuccess)
+      return fail_g(bfail(b, SV_ECUDA, "group node: %s", cudaGetErrorString(e)));
+  }
+  for (int c : rest) {
     cudaGraph_t pg = nullptr;
     int rc = fsv::ctx_capture_run(b->ctx[c], periods, &pg);
     if (rc) return fail_g(bfail(b, rc, "chain %d capture: %s", c, sv_last_error(b->ctx[c])));
@@ -285,7 +356,8 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
   }
   if (rc == SV_OK) rc = build_resident(b, res_chains, &rs);
   cudaGraphExec_t ge = nullptr;
-  if (rc == SV_OK) rc = make_graph(b, graph_chains, &rs, kPeriods, &ge);
+  std::vector<fsv::BlockGroup*> groups;
+  if (rc == SV_OK) rc = make_graph(b, graph_chains, &rs, kPeriods, &ge, &groups);
   if (rc == SV_OK) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
@@ -302,6 +374,7 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
     if (e1) cudaEventDestroy(e1);
   }
   if (ge) cudaGraphExecDestroy(ge);
+  free_groups(&groups);
   rs.release();
   for (int c : sample) {
     int r2 = reinit(b, c);
@@ -323,35 +396,33 @@ int autotune(sv_batch* b) {
     const int L = kv.first;
     std::vector<int> sample(kv.second.begin(),
                             kv.second.begin() + std::min<size_t>(8, kv.second.size()));
-    int best = SV_BATCH_PLAIN, best_tiles = kDefaultTileRun, best_n = 0;
+    int best = SV_BATCH_PLAIN, best_n = 0;
     double best_rate = -1.0;
     for (int f : {SV_BATCH_RESIDENT, SV_BATCH_BLOCK_TC, SV_BATCH_BLOCK_SIMT, SV_BATCH_PLAIN,
                   SV_BATCH_MULTIGATE}) {
       if (!form_fits(f, L)) continue;
-      for (int t : kTileRuns) {
-        // tile runs for the tensor-core form, widths for the CUDA-core one
-        if (f != SV_BATCH_BLOCK_TC && t != kDefaultTileRun) continue;
-        for (int n : kSimtWidths) {
-          if (f != SV_BATCH_BLOCK_SIMT && n != kDefaultWidth) continue;
-          if (f == SV_BATCH_BLOCK_SIMT && n > L) continue;
-          // a resident chain uses one CTA, so its form scales with the chain
-          // count up to the SM count: it is timed on every chain of this L;
-          // the other forms fill the device with one chain's passes
-          double rate = 0.0;
-          int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, t, n, &rate);
-          if (rc) return rc;
-          if (rate > best_rate) {
-            best_rate = rate;
-            best = f;
-            best_tiles = t;
-            best_n = f == SV_BATCH_BLOCK_TC ? 6 : (f == SV_BATCH_BLOCK_SIMT ? n : 0);
-          }
+      for (int n : kSimtWidths) {
+        // widths for the CUDA-core form
+        if (f != SV_BATCH_BLOCK_SIMT && n != kDefaultWidth) continue;
+        if (f == SV_BATCH_BLOCK_SIMT && n > L) continue;
+        // a resident chain uses one CTA, so its form scales with the chain
+        // count up to the SM count: it is timed on every chain of this L;
+        // the other forms fill the device with one chain's passes (the
+        // tensor-core form as one group of the sample)
+        double rate = 0.0;
+        int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, kDefaultTileRun, n,
+                           &rate);
+        if (rc) return rc;
+        if (rate > best_rate) {
+          best_rate = rate;
+          best = f;
+          best_n = f == SV_BATCH_BLOCK_TC ? 6 : (f == SV_BATCH_BLOCK_SIMT ? n : 0);
         }
       }
     }
     for (int c : kv.second) {
       b->form[c] = best;
-      b->min_tiles[c] = best_tiles;
+      b->min_tiles[c] = kDefaultTileRun;
       b->width[c] = best_n;
     }
   }
@@ -397,6 +468,7 @@ void destroy(sv_batch* b) {
   if (!b) return;
   if (b->g1) cudaGraphExecDestroy(b->g1);
   if (b->gm) cudaGraphExecDestroy(b->gm);
+  free_groups(&b->groups);
   ResidentSet rs = resident_view(b);
   rs.release();
   for (sv_ctx* c : b->ctx)
@@ -507,11 +579,11 @@ int sv_batch_evolve(sv_batch* b, int64_t periods, double* energy_out, double* no
     if (b->form[c] != SV_BATCH_RESIDENT) graph_chains.push_back(c);
   ResidentSet rs = resident_view(b);
   if (!b->g1) {
-    int rc = make_graph(b, graph_chains, &rs, 1, &b->g1);
+    int rc = make_graph(b, graph_chains, &rs, 1, &b->g1, &b->groups);
     if (rc) return rc;
   }
   if (!b->gm && periods >= b->M) {
-    int rc = make_graph(b, graph_chains, &rs, b->M, &b->gm);
+    int rc = make_graph(b, graph_chains, &rs, b->M, &b->gm, &b->groups);
     if (rc) return rc;
   }
   const int ring = fsv::ctx_ring_len();

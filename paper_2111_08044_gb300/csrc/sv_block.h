@@ -64,6 +64,21 @@ struct PassArgs {
   EpiParams ep;              // diagonal coefficients
 };
 
+// Per chain and pass of a chain group (chains whose plans share every
+// structural field: same L, windows, relabels and staging; they differ in
+// operands and measured coefficients).  The group's tensor-core pass runs
+// all chains' tiles in one launch.
+struct alignas(64) GroupChain {
+  unsigned char map_in[128];   // TMA descriptors (CUtensorMap) for this
+  unsigned char map_out[128];  // chain's state
+  const void* W = nullptr;     // the chain's operand block of this pass
+  double* partial = nullptr;   // the chain's (energy, norm) pairs, or null
+  float cx[8] = {};
+  float diag_f[5] = {};
+  float diag_lin0[8] = {};
+};
+static_assert(sizeof(GroupChain) % 64 == 0, "descriptors stay 64-byte aligned in an array");
+
 struct BlockPlan {
   int L = 0, n = 0, R = 0, split = 0;
   int start = 0;  // window of the period's first pass; the layout between periods
@@ -118,6 +133,28 @@ cudaError_t block_enqueue_period_events(BlockPlan* bp, void* psi, long long* cou
                                         cudaEvent_t* ev, bool last);
 void block_free(BlockPlan* bp);
 
+// Chain groups: tensor-core chains whose plans share every structural field
+// (same L, windows, relabels, staging orders and measured passes) run each
+// pass of all chains as one launch, and their period reduces as one.
+struct GroupMember {
+  BlockPlan* plan = nullptr;
+  void* psi = nullptr;           // the chain's state
+  long long* counter = nullptr;  // its period counter and energy ring
+  double* ring = nullptr;
+};
+struct BlockGroup;
+bool block_same_structure(const BlockPlan* a, const BlockPlan* b);
+// Descriptors, operands and coefficients of every chain and pass, and the
+// group's own partial sums ([chains][slots][grid] pairs, zeroed: only CTAs
+// that meet a chain write its pairs).
+int block_group_build(const std::vector<GroupMember>& members, int ring_len,
+                      const LaunchCfg& cfg, cudaStream_t s, BlockGroup** out, std::string* msg);
+// Window of the group's periods (0: the natural layout, no entry steps).
+int block_group_start(const BlockGroup* g);
+cudaError_t block_group_enqueue_entry(BlockGroup* g, cudaStream_t s);
+cudaError_t block_group_enqueue_period(BlockGroup* g, cudaStream_t s, bool last);
+void block_group_free(BlockGroup* g);
+
 // Nonzero if a tensor-core pass reported a timed-out wait (synchronises s).
 int block_status(BlockPlan* bp, cudaStream_t s);
 
@@ -125,6 +162,11 @@ int block_status(BlockPlan* bp, cudaStream_t s);
 cudaError_t launch_block_simt(const PassArgs& pa, void* psi, int grid, cudaStream_t s);
 cudaError_t launch_block_tc(const PassArgs& pa, void* psi, const void* map, int* status,
                             int grid, cudaStream_t s);
+// One tensor-core pass over the tiles of a chain group: pa is the pass's
+// structure with ntiles = chains x 2^nt_log2; chains: device array, one per
+// chain.  CTA b takes the contiguous tiles [b T / grid, (b + 1) T / grid).
+cudaError_t launch_block_tc_group(const PassArgs& pa, const GroupChain* chains, int nt_log2,
+                                  int* status, int grid, cudaStream_t s);
 bool block_tc_supported(int L, int n);
 cudaError_t block_tc_prepare();
 size_t block_tc_map_bytes();

@@ -43,6 +43,12 @@ void ctx_set_cyclic(sv_ctx* ctx, bool cyclic);
 int ctx_read_energies(sv_ctx* ctx, int64_t c0, int64_t count, double* e, double* n);
 // Periods the energy ring holds.
 int ctx_ring_len();
+struct BlockPlan;
+// The tensor-core block plan of a context and the device objects its
+// periods update (state, period counter, energy ring); SV_ESTATE when the
+// context has no such plan.
+int ctx_block_member(sv_ctx* ctx, BlockPlan** plan, void** psi, long long** counter,
+                     double** ring);
 
 struct Gate2 {
   int bond = 0;      // acts on sites (bond, bond + 1)

@@ -88,6 +88,17 @@ cudaError_t launch_plain_gate(int precision, void* psi, int L, int bond,
 // Sum `n` (energy, norm) partial pairs in a fixed order and record
 // (energy / (L norm), norm) at ring[(*counter) % ring_len], then ++*counter
 // (advance != 0).
+// One chain's period reduce: its partial pairs, ring and period counter.
+struct ReduceItem {
+  const double* partials = nullptr;
+  long long n = 0;
+  double* ring = nullptr;
+  long long* counter = nullptr;
+  int L = 0;
+  int ring_len = 0;
+};
+// The period reduce of `count` chains (items: device array), counters advanced.
+cudaError_t launch_period_reduce_many(const ReduceItem* items, int count, cudaStream_t s);
 cudaError_t launch_period_reduce(const double* partials, long long n, int L,
                                  double* ring, int ring_len, long long* counter,
                                  int advance, cudaStream_t s);

@@ -53,6 +53,29 @@ def test_batch_forms_match_oracle(svlib, form):
         assert err < 2e-7 * P * 4 * (cfg.L - 1) + 1e-5, (c, cfg.L, forms[c], err)
 
 
+def test_tensor_core_groups_match_oracle(svlib):
+    """Tensor-core chains of one L run as a group: each pass of all of them
+    is one launch over all their tiles, a CTA taking a contiguous range that
+    can span two chains (operand reload, coefficients and partial sums per
+    chain).  Three chains of L = 20 (384 tiles on 152 CTAs) and two of
+    L = 19, each with its own couplings and state, over 20 periods (the
+    16-period graph and single periods) against the oracle."""
+    from paper_2111_08044_gb300.sim import FloquetBatch
+    Ls = [20, 19, 20, 19, 20]
+    chains = _chains(Ls, seed=11)
+    P = 20
+    with FloquetBatch(chains, form=capi.SV_BATCH_BLOCK_TC) as b:
+        assert list(b.forms()) == [capi.SV_BATCH_BLOCK_TC] * len(chains)
+        e, n = b.evolve(P)
+        states = [b.chain_state(c) for c in range(len(chains))]
+    for c, cfg in enumerate(chains):
+        psi_o, _, e_o, n_o = orc.run_chain(cfg, periods=P)
+        np.testing.assert_allclose(e[c], e_o, atol=1e-5, rtol=0, err_msg=f"chain {c} L={cfg.L}")
+        np.testing.assert_allclose(n[c], n_o, atol=1e-5, rtol=0)
+        err = np.linalg.norm(states[c].astype(np.complex128) - psi_o)
+        assert err < 1e-4, (c, cfg.L, err)
+
+
 def test_batch_continues_across_calls(svlib):
     """Two evolve calls equal one; more periods than one graph run holds."""
     from paper_2111_08044_gb300.sim import FloquetBatch

@@ -605,7 +605,11 @@ int block_group_build(const std::vector<GroupMember>& mem, int ring_len, const L
   BlockGroup* g = new BlockGroup();
   g->m = mem;
   g->nt_log2 = lg;
-  g->grid = (int)std::min<long long>(cfg.num_sms, nt * (long long)C);
+  // one CTA per SM, each with at least kGroupMinTiles tiles (a small group
+  // then leaves SMs to the others instead of paying a CTA's set-up per tile)
+  constexpr long long kGroupMinTiles = 4;
+  g->grid = (int)std::max<long long>(
+      1, std::min<long long>(cfg.num_sms, nt * (long long)C / kGroupMinTiles));
   g->ops = ref->args;
   for (PassArgs& pa : g->ops) {
     pa.ntiles = nt * (long long)C;

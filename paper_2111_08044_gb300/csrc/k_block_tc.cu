@@ -960,16 +960,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                       (uint32_t)((issued / kSlots - 1) & 1), abort, status))
           break;
         if ((issued & 3) == 0 && new_chain(issued >> 2)) {
-          // a new chain: its descriptors, and its operand block once the
-          // MMAs of the previous chain are done
-          if (!wait_bar(mbase + kBarWFree, (uint32_t)(wload & 1), abort, status)) break;
-          const GroupChain& gc = grp[chain_of(issued >> 2)];
-          map_in = reinterpret_cast<const CUtensorMap*>(gc.map_in);
+          // a new chain: its descriptors for the boxes from here on
+          map_in = reinterpret_cast<const CUtensorMap*>(grp[chain_of(issued >> 2)].map_in);
           tensormap_acquire(map_in);
-          load_w(gc.W);
-          ++wload;
         }
         load_box(issued);
+        if ((issued & 3) == 3 && new_chain(issued >> 2)) {
+          // and its operand block, once the new chain's first tile is on its
+          // way and the MMAs of the previous chain are done with the old one
+          if (!wait_bar(mbase + kBarWFree, (uint32_t)(wload & 1), abort, status)) {
+            ++issued;
+            break;
+          }
+          load_w(grp[chain_of(issued >> 2)].W);
+          ++wload;
+        }
       }
       if (*abort) {
         // drain copies nobody will consume before the CTA exits

@@ -228,22 +228,19 @@ int sv_renormalize(sv_ctx *ctx, double *norm2_before);
 
 /*
  * Reverse-mode gradient of the final energy density f = <psi_P|H0|psi_P>/L
- * with respect to the per-period kick angles theta_p and fields hx_p
- * (p = 0..P-1, P = n_period_params, plain mode).  Starting from the current
- * state it evolves P periods forward without storing states, seeds
+ * after P = `periods` periods with respect to the per-period kick angles
+ * theta_p and fields hx_p of those periods (p = 0..P-1; plain mode, built
+ * with n_period_params >= P, period counter at 0).  Starting from the
+ * current state it evolves P periods forward without storing states, seeds
  * lambda = (H0/L) psi_P, and walks the gates backwards, un-applying each on
  * psi and lambda while accumulating 2 Re <lambda| dG G^dagger |psi>.  On
  * return the state buffer holds psi back at its starting point up to
- * rounding.  grad_theta / grad_hx: host, length P (nullable).
- * energy_density (nullable): f.  Needs 2x the state memory for lambda,
- * allocated by the library.  The number of periods is not an argument:
- * the gradient is taken with respect to every per-period parameter, so P is
- * the length of the theta_p / hx_p arrays given to sv_build_floquet
- * (n_period_params); to differentiate fewer periods, build with shorter
- * arrays.  Errors: SV_EINVAL, SV_ESTATE, SV_ENOMEM, SV_ECUDA,
- * SV_EUNSUPPORTED.
+ * rounding and the counter is 0.  grad_theta / grad_hx: host, length P
+ * (nullable).  energy_density (nullable): f.  Needs 2x the state memory for
+ * lambda, allocated by the library.  Errors: SV_EINVAL (periods outside
+ * 1..n_period_params), SV_ESTATE, SV_ENOMEM, SV_ECUDA, SV_EUNSUPPORTED.
  */
-int sv_adjoint(sv_ctx *ctx, double *grad_theta, double *grad_hx,
+int sv_adjoint(sv_ctx *ctx, int64_t periods, double *grad_theta, double *grad_hx,
                double *energy_density);
 
 /* Copy the state, natural layout, to `host_dst`: host memory or device

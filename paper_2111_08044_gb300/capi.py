@@ -87,7 +87,7 @@ SIGNATURES = {
     "sv_evolve_profiled": ([_vp, _i64, _dp, _dp, _dp], _i32),
     "sv_expect_energy": ([_vp, _dp, _dp], _i32),
     "sv_renormalize": ([_vp, _dp], _i32),
-    "sv_adjoint": ([_vp, _dp, _dp, _dp], _i32),
+    "sv_adjoint": ([_vp, _i64, _dp, _dp, _dp], _i32),
     "sv_get_state": ([_vp, _vp, _sz], _i32),
     "sv_set_state": ([_vp, _vp, _sz, _i64], _i32),
     "sv_save": ([_vp, ctypes.c_char_p], _i32),

@@ -802,7 +802,7 @@ int no_df(sv_ctx* ctx, const char* what) {
 
 extern "C" {
 
-int sv_version(void) { return 1; }
+int sv_version(void) { return 2; }
 
 int sv_create(sv_ctx** out, int device, int precision, void* cuda_stream) {
   if (!out) return SV_EINVAL;
@@ -1195,7 +1195,8 @@ int sv_renormalize(sv_ctx* ctx, double* norm2_before) {
   return SV_OK;
 }
 
-int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_density) {
+int sv_adjoint(sv_ctx* ctx, int64_t periods, double* grad_theta, double* grad_hx,
+               double* energy_density) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   rc = ensure_natural(ctx);  // a state kept in the period layout
@@ -1205,11 +1206,14 @@ int sv_adjoint(sv_ctx* ctx, double* grad_theta, double* grad_hx, double* energy_
     return fail(ctx, SV_EUNSUPPORTED, "the adjoint needs SV_MODE_PLAIN");
   if (ctx->n_period_params <= 0)
     return fail(ctx, SV_ESTATE, "the adjoint needs per-period parameters (n_period_params > 0)");
+  if (periods < 1 || periods > ctx->n_period_params)
+    return fail(ctx, SV_EINVAL, "periods=%lld outside 1..%lld (the per-period parameters)",
+                (long long)periods, (long long)ctx->n_period_params);
   if (ctx->counter != 0)
     return fail(ctx, SV_ESTATE, "the adjoint starts at period 0 (counter is %lld)",
                 (long long)ctx->counter);
   const int L = ctx->L;
-  const int64_t P = ctx->n_period_params;
+  const int64_t P = periods;
   const bool c128 = ctx->precision == SV_C128;
   const size_t cb = amp_bytes(ctx->precision);
   DeviceGuard dg(ctx->device);

@@ -154,12 +154,15 @@ class FloquetSimulator:
                    "sv_renormalize")
         return n.value
 
-    def adjoint(self) -> Tuple[np.ndarray, np.ndarray, float]:
-        P = self._n_period_params()
-        gt = np.zeros(P)
-        gh = np.zeros(P)
+    def adjoint(self, periods: Optional[int] = None) -> Tuple[np.ndarray, np.ndarray, float]:
+        """Gradients of the energy density after `periods` periods (default:
+        all per-period parameters) with respect to those periods' kick angles
+        and fields, and that energy density."""
+        P = self._n_period_params() if periods is None else int(periods)
+        gt = np.zeros(max(P, 0))
+        gh = np.zeros(max(P, 0))
         e = ctypes.c_double()
-        capi.check(self._lib.sv_adjoint(self._ctx, gt.ctypes.data_as(capi._dp),
+        capi.check(self._lib.sv_adjoint(self._ctx, P, gt.ctypes.data_as(capi._dp),
                                         gh.ctypes.data_as(capi._dp), ctypes.byref(e)),
                    self._ctx, "sv_adjoint")
         return gt, gh, e.value

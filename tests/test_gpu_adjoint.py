@@ -116,6 +116,28 @@ def test_adjoint_L20_200_periods_directional(svlib):
     assert np.abs(gh32 - gh).max() < 1e-3 * scale
 
 
+def test_adjoint_over_fewer_periods_than_parameters(svlib):
+    """sv_adjoint(periods = P' < n_period_params) differentiates the energy
+    after P' periods: the oracle's adjoint of the first P' periods."""
+    from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
+    cfg = _cfg(8, 5, seed=21)
+    with FloquetSimulator(cfg.L, precision="c128") as sim:
+        sim.init_product_state(cfg.spinors())
+        sim.build(**chain_params(cfg))
+        gt, gh, e = sim.adjoint(periods=3)
+        for bad in (0, 6):
+            with pytest.raises(capi.SvError) as ei:
+                sim.adjoint(periods=bad)
+            assert ei.value.code == capi.SV_EINVAL
+    short = inputs.ChainConfig(L=cfg.L, periods=3, seed=cfg.seed, first_layer=cfg.first_layer,
+                               edge_field_weight=cfg.edge_field_weight,
+                               theta_p=cfg.theta_p[:3], hx_p=cfg.hx_p[:3])
+    ot, oh, oe = _oracle_adjoint(short)
+    assert gt.shape == (3,) and abs(e - oe) < 1e-12
+    np.testing.assert_allclose(gt, ot, atol=1e-11, rtol=1e-10)
+    np.testing.assert_allclose(gh, oh, atol=1e-11, rtol=1e-10)
+
+
 def test_adjoint_call_order(svlib):
     from paper_2111_08044_gb300.sim import FloquetSimulator, chain_params
     cfg = _cfg(8, 3, seed=1)

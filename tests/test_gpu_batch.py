@@ -57,11 +57,12 @@ def test_tensor_core_groups_match_oracle(svlib):
     """Tensor-core chains of one L run as a group: each pass of all of them
     is one launch over all their tiles, a CTA taking a contiguous range that
     can span two chains (operand reload, coefficients and partial sums per
-    chain).  Three chains of L = 20 (384 tiles on 152 CTAs) and two of
-    L = 19, each with its own couplings and state, over 20 periods (the
-    16-period graph and single periods) against the oracle."""
+    chain).  Five chains of L = 20 (640 tiles on 152 CTAs, 3 of them
+    spanning two chains) and ten of L = 19 (640 tiles, 6 CTAs spanning),
+    interleaved, each with its own couplings and state, over 20 periods
+    (the 16-period graph and single periods) against the oracle."""
     from paper_2111_08044_gb300.sim import FloquetBatch
-    Ls = [20, 19, 20, 19, 20]
+    Ls = [20, 19, 19] * 5
     chains = _chains(Ls, seed=11)
     P = 20
     with FloquetBatch(chains, form=capi.SV_BATCH_BLOCK_TC) as b:

@@ -680,6 +680,8 @@ int block_group_build(const std::vector<GroupMember>& mem, int ring_len, const L
 
 int block_group_start(const BlockGroup* g) { return g->m[0].plan->start; }
 
+size_t block_group_size(const BlockGroup* g) { return g->m.size(); }
+
 namespace {
 cudaError_t group_pass(BlockGroup* g, int k, cudaStream_t s) {
   return launch_block_tc_group(g->ops[k], g->d_chains + (size_t)k * g->m.size(), g->nt_log2,

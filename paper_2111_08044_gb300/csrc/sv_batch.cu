@@ -283,11 +283,19 @@ int make_graph(sv_batch* b, const std::vector<int>& chains, const ResidentSet* r
     int rc = make_groups(b, chains, &rest, groups);
     if (rc) return fail_g(rc);
   } else {
+    // the groups were built for these chains by an earlier call
+    size_t grouped = 0;
     for (int c : chains) {
       fsv::GroupMember m;
       if (fsv::ctx_block_member(b->ctx[c], &m.plan, &m.psi, &m.counter, &m.ring) != SV_OK)
         rest.push_back(c);
+      else
+        ++grouped;
     }
+    size_t members = 0;
+    for (fsv::BlockGroup* grp : *groups) members += fsv::block_group_size(grp);
+    if (members != grouped)
+      return fail_g(bfail(b, SV_ESTATE, "chain groups built for another set of chains"));
   }
   for (fsv::BlockGroup* grp : *groups) {
     cudaGraph_t pg = nullptr;

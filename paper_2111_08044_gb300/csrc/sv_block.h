@@ -151,6 +151,8 @@ int block_group_build(const std::vector<GroupMember>& members, int ring_len,
                       const LaunchCfg& cfg, cudaStream_t s, BlockGroup** out, std::string* msg);
 // Window of the group's periods (0: the natural layout, no entry steps).
 int block_group_start(const BlockGroup* g);
+// Chains in the group.
+size_t block_group_size(const BlockGroup* g);
 cudaError_t block_group_enqueue_entry(BlockGroup* g, cudaStream_t s);
 cudaError_t block_group_enqueue_period(BlockGroup* g, cudaStream_t s, bool last);
 void block_group_free(BlockGroup* g);

@@ -52,6 +52,9 @@ def _parse():
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-breakdown", action="store_true",
+                    help="time each L group of the 512-chain batch alone against its HBM bound "
+                         "(one JSON line per L) instead of the default line")
     ap.add_argument("--batch-periods", type=int, default=2000,
                     help="periods of the 512-chain batch line (the config's 2000; 0 skips it)")
     return ap.parse_args()
@@ -488,6 +491,44 @@ def _config(args, world):
             "l2": l2}
 
 
+def run_batch_breakdown(args):
+    """Each L group of the 512-chain preset run alone in the form the full
+    batch gives it (resident at L <= 14, tensor-core groups above): ms per
+    period of the group against its HBM bound, one JSON line per L."""
+    import numpy as np
+    import torch
+
+    from paper_2111_08044_gb300 import capi, inputs
+    from paper_2111_08044_gb300.sim import FloquetBatch
+
+    hbm_gbs = _peaks()[0]
+    chains = inputs.batch_preset(512)
+    periods = 64
+    for L in sorted({c.L for c in chains}):
+        group = [c for c in chains if c.L == L]
+        form = capi.SV_BATCH_RESIDENT if L <= 14 else capi.SV_BATCH_BLOCK_TC
+        b = FloquetBatch(group, form=form)
+        b.evolve(16)
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(b.stream)
+        b.evolve(periods)
+        end.record(b.stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end) / periods
+        forms, widths = b.forms(), b.widths()
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        bound = _batch_hbm_bound_ms(group, forms, widths, hbm_gbs)
+        print(json.dumps({"batch_breakdown": True, "L": L, "chains": len(group),
+                          "form": "resident" if form == capi.SV_BATCH_RESIDENT else "block_tc group",
+                          "ms_per_period": ms, "hbm_bound_ms_per_period": bound,
+                          "hbm_bound_frac": bound / ms if bound else None}), flush=True)
+    return 0
+
+
 def run_oracle_table(args):
     """The oracle's CPU-baseline table: whole periods at several chain
     lengths, all cores and one thread (one JSON line per entry)."""
@@ -591,6 +632,8 @@ def main():
     args = _parse()
     if args.oracle_table:
         return run_oracle_table(args)
+    if args.batch_breakdown:
+        return run_batch_breakdown(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -44,7 +44,6 @@ struct sv_batch {
   std::vector<int> L;
   std::vector<size_t> off;
   std::vector<int> form;
-  std::vector<int> min_tiles;  // block forms: tiles per CTA at least
   std::vector<int> width;      // block forms: window width n
   std::vector<sv_floquet_params> params;
   std::vector<const double*> spinors;  // caller's arrays, valid during create only
@@ -189,9 +188,10 @@ int build_resident(sv_batch* b, const std::vector<int>& chains, ResidentSet* rs)
 }
 
 // Build the period evolution of chain c in its context for a graph form
-// (block forms: window width n, at least min_tiles tiles per CTA).
-int build_graph_form(sv_batch* b, int c, int form, int min_tiles, int n) {
-  fsv::ctx_set_min_tiles(b->ctx[c], min_tiles);
+// (block forms: window width n; CUDA-core passes keep kDefaultTileRun tiles
+// per CTA at least).
+int build_graph_form(sv_batch* b, int c, int form, int n) {
+  fsv::ctx_set_min_tiles(b->ctx[c], kDefaultTileRun);
   sv_floquet_params p = b->params[c];
   p.theta_p = nullptr;
   p.hx_p = nullptr;
@@ -345,10 +345,10 @@ int reinit(sv_batch* b, int c) {
 }
 
 // Chain-periods per second of the chains `sample` run together, chain
-// sample[i] in form forms[i] (block forms with at least tiles[i] tiles per
-// CTA).  The trial moves the states; they are initialised again after it.
-int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<int>& forms,
-               const std::vector<int>& tiles, int n, double* rate) {
+// sample[i] in form forms[i] (the CUDA-core block form at width n).  The
+// trial moves the states; they are initialised again after it.
+int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<int>& forms, int n,
+               double* rate) {
   *rate = 0.0;
   constexpr int kPeriods = 4;
   ResidentSet rs;
@@ -358,7 +358,7 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
     if (forms[i] == SV_BATCH_RESIDENT) {
       res_chains.push_back(sample[i]);
     } else {
-      rc = build_graph_form(b, sample[i], forms[i], tiles[i], n);
+      rc = build_graph_form(b, sample[i], forms[i], n);
       graph_chains.push_back(sample[i]);
     }
   }
@@ -391,10 +391,8 @@ int time_forms(sv_batch* b, const std::vector<int>& sample, const std::vector<in
   return rc;
 }
 
-int time_form(sv_batch* b, const std::vector<int>& sample, int form, int min_tiles, int n,
-              double* rate) {
-  return time_forms(b, sample, std::vector<int>(sample.size(), form),
-                    std::vector<int>(sample.size(), min_tiles), n, rate);
+int time_form(sv_batch* b, const std::vector<int>& sample, int form, int n, double* rate) {
+  return time_forms(b, sample, std::vector<int>(sample.size(), form), n, rate);
 }
 
 int autotune(sv_batch* b) {
@@ -418,8 +416,7 @@ int autotune(sv_batch* b) {
         // the other forms fill the device with one chain's passes (the
         // tensor-core form as one group of the sample)
         double rate = 0.0;
-        int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, kDefaultTileRun, n,
-                           &rate);
+        int rc = time_form(b, f == SV_BATCH_RESIDENT ? kv.second : sample, f, n, &rate);
         if (rc) return rc;
         if (rate > best_rate) {
           best_rate = rate;
@@ -430,7 +427,6 @@ int autotune(sv_batch* b) {
     }
     for (int c : kv.second) {
       b->form[c] = best;
-      b->min_tiles[c] = kDefaultTileRun;
       b->width[c] = best_n;
     }
   }
@@ -443,7 +439,7 @@ int setup(sv_batch* b) {
     if (b->form[c] == SV_BATCH_RESIDENT) {
       b->res.push_back(c);
     } else {
-      int rc = build_graph_form(b, c, b->form[c], b->min_tiles[c],
+      int rc = build_graph_form(b, c, b->form[c],
                                 b->width[c] > 0 ? b->width[c] : kDefaultWidth);
       if (rc) return rc;
     }
@@ -547,7 +543,6 @@ int sv_batch_create(sv_batch** out, int device, int n_chains, const int* L,
   }
   if (rc == SV_OK) {
     b->form.assign(n_chains, SV_BATCH_PLAIN);
-    b->min_tiles.assign(n_chains, kDefaultTileRun);
     b->width.assign(n_chains, 0);
     if (form == SV_BATCH_AUTO) {
       rc = autotune(b);
